@@ -1,0 +1,168 @@
+/*
+ * rime.h -- C ABI of librime: GPU RIME predict fused with a weighted chi^2
+ * (Montblanc, arXiv 1501.07719), for NVIDIA GB300 (sm_103a).
+ *
+ * The library evaluates, for every timestep t, baseline (p, q) and channel k,
+ *
+ *   V_tpqk = G_tpk ( sum_s E_tpsk K_tpsk B_sk K_tqsk^H E_tqsk^H ) G_tqk^H   (eq. 1)
+ *   B_sk   = (nu_k / nu_ref)^alpha_s [[I+Q, U+iV], [U-iV, I-Q]] * g_spqk    (eq. 2)
+ *   K_tpsk = exp(2 pi i (u l + v m + w (n - 1)) nu_k / c)                  (eq. 3)
+ *   E_tpsk = cos^3(C nu_k[GHz] |l_s - dl_tp|), zero past the first null      (eq. 4)
+ *
+ * with g the Gaussian shape factor (1 for point sources; the Fourier
+ * transform of a unit-flux elliptical Gaussian of FWHM axes (major, minor) and
+ * position angle pa from +m towards +l, at the baseline (u_p-u_q, v_p-v_q)/lambda)
+ * and reduces it, in the same kernel, to
+ *
+ *   chi^2 = sum_{t,pq,k} w_tpqk sum_c |V_tpqk,c - D_tpqk,c|^2              (eq. 7)
+ *
+ * Conventions used by every entry point:
+ *  - Baselines are the pairs p < q in row-major upper-triangle order:
+ *    bl(p, q) = p*na - p*(p+1)/2 + (q - p - 1); nbl = na*(na-1)/2 (Sec. 2.2:
+ *    autocorrelations are discarded).
+ *  - Correlations: the 2x2 matrix in row-major order (00, 01, 10, 11).
+ *  - Complex numbers are interleaved (re, im). "complex" below means complex64
+ *    (2 x float) in RIME_FP32 mode and complex128 (2 x double) in RIME_FP64.
+ *  - Array order is time slowest, channel (then correlation) fastest, as in
+ *    Sec. 4.1: vis/data [ntime][nbl][nchan][4], weight [ntime][nbl][nchan].
+ *  - Source parameters, uvw, frequencies, pointing and gains are always
+ *    double precision, whatever the compute precision.
+ *  - Input pointers may be host (pageable or pinned) or device pointers; the
+ *    library copies what it needs into buffers it owns and the caller keeps
+ *    ownership of its arrays. Output pointers are device pointers unless
+ *    stated otherwise.
+ *  - All work is ordered on the CUDA stream given to rime_create. Only the
+ *    calls that return a host value (rime_create, rime_chi2, rime_chi2_grad,
+ *    rime_sync) wait for the stream.
+ *  - Every call returns a status and never aborts. On error the outputs are
+ *    left untouched and rime_last_error() describes the cause.
+ *  - Input values are checked on the GPU as they are uploaded (NaN/Inf,
+ *    l^2+m^2 >= 1, major < minor or negative axes, negative weights,
+ *    frequencies <= 0). A failed check makes every later kernel skip its
+ *    work; the status is returned by the next call that waits for the stream
+ *    (rime_chi2, rime_chi2_grad, rime_sync), until the offending input is set
+ *    again with valid values.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef RIME_H
+#define RIME_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rime_ctx rime_ctx;
+
+typedef enum {
+    RIME_OK = 0,
+    RIME_E_INVALID = 1,   /* bad argument: size, pointer or value out of range */
+    RIME_E_STATE = 2,     /* call out of order (e.g. rime_chi2 before rime_set_sources) */
+    RIME_E_OOM = 3,       /* a device allocation failed */
+    RIME_E_CUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+    RIME_E_TIMEOUT = 5,   /* a bounded wait inside a kernel gave up */
+    RIME_E_NONFINITE = 6  /* NaN or Inf in an input array */
+} rime_status;
+
+typedef enum {
+    RIME_FP32 = 0,        /* FP32 arithmetic; phase reduced exactly in double-float; FP64 chi^2 sums */
+    RIME_FP64 = 1         /* FP64 throughout */
+} rime_precision;
+
+/* Problem dimensions (Table 1) and the two model constants. */
+typedef struct {
+    int32_t na;           /* antennas, >= 2 */
+    int32_t ntime;        /* timesteps, >= 1 */
+    int32_t nchan;        /* channels, >= 1 */
+    int32_t precision;    /* rime_precision */
+    double ref_freq_hz;   /* nu_ref of eq. 2 (> 0); 1.4e9 in the paper's sample code */
+    double beam_c;        /* C of eq. 4 in rad^-1 GHz^-1 (>= 0); 65 for WSRT */
+} rime_dims;
+
+/* A sky model (Table 2: lm, brightness, gaussian shapes), structure of
+ * arrays, double precision, host or device pointers. */
+typedef struct {
+    int32_t nsrc;         /* >= 0 */
+    int32_t time_varying; /* 0: stokes [nsrc][4]; 1: stokes [ntime][nsrc][4] (Table 2) */
+    const double *lm;     /* [nsrc][2] direction cosines (l, m), l^2 + m^2 < 1 */
+    const double *stokes; /* Stokes (I, Q, U, V) in Jy at nu_ref */
+    const double *alpha;  /* [nsrc] spectral index (eq. 2) */
+    const double *shape;  /* [nsrc][3] (major FWHM, minor FWHM, pa) in rad,
+                             major >= minor >= 0; (0, 0, *) is a point source.
+                             NULL: all sources are points. */
+} rime_sources;
+
+/* Number of baselines na*(na-1)/2 (Sec. 2.2). */
+int64_t rime_nbl(int32_t na);
+
+/* Human-readable name of a status code. Never NULL. */
+const char *rime_status_string(rime_status s);
+
+/* Creates a context: validates dims, allocates the device buffers the
+ * problem needs and uploads the observation (Table 2 inputs from the
+ * measurement set). Waits for the stream.
+ *   ctx       out: the new context (NULL on failure)
+ *   dims      problem dimensions and model constants
+ *   freq_hz   [nchan] channel frequencies, > 0
+ *   uvw       [ntime][na][3] antenna coordinates in metres
+ *   pointing  [ntime][na][2] pointing errors (dl, dm) in rad, or NULL (none)
+ *   data      [ntime][nbl][nchan][4] complex observed visibilities, or NULL
+ *             (rime_predict still works; rime_chi2 needs data)
+ *   weight    [ntime][nbl][nchan] float (FP32) / double (FP64), >= 0, or NULL
+ *             (unit weights)
+ *   cuda_stream  cudaStream_t to order all work on (NULL: legacy default stream)
+ * Errors: RIME_E_INVALID (sizes, NULL required pointers, invalid values in
+ * freq/uvw/data/weight), RIME_E_NONFINITE, RIME_E_OOM, RIME_E_CUDA. */
+rime_status rime_create(rime_ctx **ctx, const rime_dims *dims, const double *freq_hz,
+                        const double *uvw, const double *pointing, const void *data,
+                        const void *weight, void *cuda_stream);
+
+/* Replaces uvw [ntime][na][3] and pointing [ntime][na][2] (NULL: none). */
+rime_status rime_set_uvw(rime_ctx *ctx, const double *uvw, const double *pointing);
+
+/* Replaces the observed data and weights (same layouts as rime_create;
+ * weight NULL: unit weights). */
+rime_status rime_set_data(rime_ctx *ctx, const void *data, const void *weight);
+
+/* Sets the direction-independent gains G_tpk of eq. 1:
+ * [ntime][na][nchan][4] complex128 (the 2x2 Jones matrix, row-major), or NULL
+ * for identity gains (the default). */
+rime_status rime_set_gains(rime_ctx *ctx, const double *gains);
+
+/* Sets the sky model (Table 2) and precomputes the per-source and
+ * per-(time, source, antenna) factors of eqs. 2-4 on the GPU. Does not wait. */
+rime_status rime_set_sources(rime_ctx *ctx, const rime_sources *src);
+
+/* Model visibilities V (eq. 1) for every (t, bl, k): writes
+ * vis_out [ntime][nbl][nchan][4] complex (device pointer, caller-owned).
+ * Algorithms 1-2 with the per-antenna factors kept on chip. Does not wait. */
+rime_status rime_predict(rime_ctx *ctx, void *vis_out);
+
+/* chi^2 of eq. 7 (without the ln-weight term), fused with the predict: the
+ * visibilities are never written to memory. Waits for the stream and stores
+ * the value in *chi2 (host pointer). Requires data. */
+rime_status rime_chi2(rime_ctx *ctx, double *chi2);
+
+/* As rime_chi2 but leaves the result in device memory (*chi2_dev, one
+ * double) and does not wait; suitable for CUDA graph capture. */
+rime_status rime_chi2_async(rime_ctx *ctx, double *chi2_dev);
+
+/* sum over visibilities of ln(2 pi / w) (the second term of eq. 7), so that
+ * -2 ln L = chi^2 + rime_ln_norm. Waits for the stream. */
+rime_status rime_ln_norm(rime_ctx *ctx, double *ln_norm);
+
+/* Waits for all work on the context's stream and returns any deferred
+ * status (failed input checks, kernel errors). */
+rime_status rime_sync(rime_ctx *ctx);
+
+/* The message for the last failed call on this context ("" if none). */
+const char *rime_last_error(const rime_ctx *ctx);
+
+/* Frees the context and its device buffers. NULL is ignored. */
+void rime_destroy(rime_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIME_H */

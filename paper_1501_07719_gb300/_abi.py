@@ -1,0 +1,211 @@
+"""ctypes binding of librime.so (include/rime.h).
+
+Argument marshalling only: every computation runs in the CUDA library. Arrays
+may be numpy arrays (host memory) or torch tensors (host or device); they must
+be C-contiguous with the dtype the ABI states. Errors raise RimeError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librime.so")
+
+RIME_OK, RIME_E_INVALID, RIME_E_STATE, RIME_E_OOM, RIME_E_CUDA, RIME_E_TIMEOUT, RIME_E_NONFINITE = range(7)
+RIME_FP32, RIME_FP64 = 0, 1
+
+
+class rime_dims(C.Structure):
+    _fields_ = [("na", C.c_int32), ("ntime", C.c_int32), ("nchan", C.c_int32),
+                ("precision", C.c_int32), ("ref_freq_hz", C.c_double), ("beam_c", C.c_double)]
+
+
+class rime_sources(C.Structure):
+    _fields_ = [("nsrc", C.c_int32), ("time_varying", C.c_int32), ("lm", C.c_void_p),
+                ("stokes", C.c_void_p), ("alpha", C.c_void_p), ("shape", C.c_void_p)]
+
+
+class RimeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{status_string(status)}: {message}")
+
+
+_lib = None
+
+
+def lib():
+    """The loaded librime.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1501_07719_gb300.build` (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        vp, ip = C.c_void_p, C.c_int
+        L.rime_nbl.argtypes, L.rime_nbl.restype = [C.c_int32], C.c_int64
+        L.rime_status_string.argtypes, L.rime_status_string.restype = [ip], C.c_char_p
+        L.rime_last_error.argtypes, L.rime_last_error.restype = [vp], C.c_char_p
+        L.rime_create.argtypes = [C.POINTER(vp), C.POINTER(rime_dims), vp, vp, vp, vp, vp, vp]
+        L.rime_set_uvw.argtypes = [vp, vp, vp]
+        L.rime_set_data.argtypes = [vp, vp, vp]
+        L.rime_set_gains.argtypes = [vp, vp]
+        L.rime_set_sources.argtypes = [vp, C.POINTER(rime_sources)]
+        L.rime_predict.argtypes = [vp, vp]
+        L.rime_chi2.argtypes = [vp, C.POINTER(C.c_double)]
+        L.rime_chi2_async.argtypes = [vp, vp]
+        L.rime_ln_norm.argtypes = [vp, C.POINTER(C.c_double)]
+        L.rime_sync.argtypes = [vp]
+        L.rime_destroy.argtypes, L.rime_destroy.restype = [vp], None
+        for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
+                  "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async",
+                  "rime_ln_norm", "rime_sync"):
+            getattr(L, f).restype = ip
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().rime_status_string(s).decode()
+    except RuntimeError:
+        return f"status {s}"
+
+
+def _check(status: int, ctx=None):
+    if status != RIME_OK:
+        msg = lib().rime_last_error(ctx).decode()
+        raise RimeError(status, msg)
+
+
+# ---------------------------------------------------------------------------
+# array marshalling
+# ---------------------------------------------------------------------------
+_TORCH_DT = {}
+
+
+def _torch():
+    import torch
+    if not _TORCH_DT:
+        _TORCH_DT.update({np.dtype(np.float32): torch.float32, np.dtype(np.float64): torch.float64,
+                          np.dtype(np.complex64): torch.complex64, np.dtype(np.complex128): torch.complex128,
+                          np.dtype(np.int32): torch.int32})
+    return torch
+
+
+class _Keep:
+    """Keeps host copies alive for the duration of a call."""
+
+    def __init__(self):
+        self.refs = []
+
+    def ptr(self, x, dtype, name):
+        if x is None:
+            return None
+        dtype = np.dtype(dtype)
+        if isinstance(x, np.ndarray) or np.isscalar(x) or isinstance(x, (list, tuple)):
+            a = np.ascontiguousarray(x, dtype=dtype)
+            self.refs.append(a)
+            return a.ctypes.data
+        torch = _torch()
+        if isinstance(x, torch.Tensor):
+            if x.dtype != _TORCH_DT[dtype]:
+                raise TypeError(f"{name}: expected {_TORCH_DT[dtype]}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError(f"{name}: tensor must be contiguous")
+            return x.data_ptr()
+        raise TypeError(f"{name}: unsupported array type {type(x)}")
+
+
+def _ctype(precision):
+    return (np.complex128, np.float64) if precision == RIME_FP64 else (np.complex64, np.float32)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one function per entry point
+# ---------------------------------------------------------------------------
+def rime_nbl(na: int) -> int:
+    return lib().rime_nbl(na)
+
+
+def rime_create(na, ntime, nchan, precision, freq_hz, uvw, pointing=None, data=None,
+                weight=None, stream=0, ref_freq_hz=1.4e9, beam_c=65.0):
+    """Returns an opaque context handle (int). stream: a cudaStream_t as int."""
+    L = lib()
+    dims = rime_dims(na, ntime, nchan, precision, ref_freq_hz, beam_c)
+    cd, rd = _ctype(precision)
+    k = _Keep()
+    ctx = C.c_void_p()
+    s = L.rime_create(C.byref(ctx), C.byref(dims), k.ptr(freq_hz, np.float64, "freq_hz"),
+                      k.ptr(uvw, np.float64, "uvw"), k.ptr(pointing, np.float64, "pointing"),
+                      k.ptr(data, cd, "data"), k.ptr(weight, rd, "weight"), stream or None)
+    _check(s, None)
+    return ctx.value
+
+
+def rime_set_uvw(ctx, uvw, pointing=None):
+    k = _Keep()
+    _check(lib().rime_set_uvw(ctx, k.ptr(uvw, np.float64, "uvw"), k.ptr(pointing, np.float64, "pointing")), ctx)
+
+
+def rime_set_data(ctx, precision, data, weight=None):
+    cd, rd = _ctype(precision)
+    k = _Keep()
+    _check(lib().rime_set_data(ctx, k.ptr(data, cd, "data"), k.ptr(weight, rd, "weight")), ctx)
+
+
+def rime_set_gains(ctx, gains):
+    k = _Keep()
+    _check(lib().rime_set_gains(ctx, k.ptr(gains, np.complex128, "gains")), ctx)
+
+
+def make_sources(lm, stokes, alpha, shape=None, keep: _Keep | None = None) -> rime_sources:
+    k = keep if keep is not None else _Keep()
+    nsrc = int(alpha.shape[0])
+    tv = 1 if len(stokes.shape) == 3 else 0
+    return rime_sources(nsrc, tv, k.ptr(lm, np.float64, "lm"), k.ptr(stokes, np.float64, "stokes"),
+                        k.ptr(alpha, np.float64, "alpha"), k.ptr(shape, np.float64, "shape"))
+
+
+def rime_set_sources(ctx, lm, stokes, alpha, shape=None):
+    k = _Keep()
+    src = make_sources(lm, stokes, alpha, shape, k)
+    _check(lib().rime_set_sources(ctx, C.byref(src)), ctx)
+
+
+def rime_predict(ctx, vis_out):
+    """vis_out: a device tensor [ntime][nbl][nchan][4] of the context's complex type."""
+    _check(lib().rime_predict(ctx, vis_out.data_ptr()), ctx)
+
+
+def rime_chi2(ctx) -> float:
+    out = C.c_double()
+    _check(lib().rime_chi2(ctx, C.byref(out)), ctx)
+    return out.value
+
+
+def rime_chi2_async(ctx, chi2_dev):
+    """chi2_dev: a float64 device tensor with at least one element."""
+    _check(lib().rime_chi2_async(ctx, chi2_dev.data_ptr()), ctx)
+
+
+def rime_ln_norm(ctx) -> float:
+    out = C.c_double()
+    _check(lib().rime_ln_norm(ctx, C.byref(out)), ctx)
+    return out.value
+
+
+def rime_sync(ctx):
+    _check(lib().rime_sync(ctx), ctx)
+
+
+def rime_last_error(ctx) -> str:
+    return lib().rime_last_error(ctx).decode()
+
+
+def rime_destroy(ctx):
+    if ctx:
+        lib().rime_destroy(ctx)

@@ -1,0 +1,80 @@
+"""A Python handle around one librime context, using torch for device memory
+and streams."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _abi as A
+
+
+class Rime:
+    """One observation on the GPU.
+
+    obs: dict with na, ntime, nchan, freq, uvw, pointing (or None),
+         ref_freq_hz, beam_c; data / weight may be given here or later.
+    precision: RIME_FP32 or RIME_FP64.
+    """
+
+    def __init__(self, obs: dict, precision: int = A.RIME_FP32, data=None, weight=None, stream=None):
+        import torch
+        self.torch = torch
+        self.precision = precision
+        self.na, self.ntime, self.nchan = int(obs["na"]), int(obs["ntime"]), int(obs["nchan"])
+        self.nbl = self.na * (self.na - 1) // 2
+        self.cdtype = torch.complex128 if precision == A.RIME_FP64 else torch.complex64
+        self.rdtype = torch.float64 if precision == A.RIME_FP64 else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = A.rime_create(self.na, self.ntime, self.nchan, precision, obs["freq"], obs["uvw"],
+                                 obs.get("pointing"), data, weight, self.stream.cuda_stream,
+                                 float(obs["ref_freq_hz"]), float(obs["beam_c"]))
+
+    # inputs ---------------------------------------------------------------
+    def set_uvw(self, uvw, pointing=None):
+        A.rime_set_uvw(self.ctx, uvw, pointing)
+
+    def set_data(self, data, weight=None):
+        A.rime_set_data(self.ctx, self.precision, data, weight)
+
+    def set_gains(self, gains):
+        A.rime_set_gains(self.ctx, gains)
+
+    def set_sources(self, src: dict):
+        A.rime_set_sources(self.ctx, src["lm"], src["stokes"], src["alpha"], src.get("shape"))
+
+    # calls ------------------------------------------------------------------
+    def predict(self, out=None):
+        if out is None:
+            out = self.torch.empty((self.ntime, self.nbl, self.nchan, 4), dtype=self.cdtype,
+                                   device="cuda")
+        A.rime_predict(self.ctx, out)
+        return out
+
+    def chi2(self) -> float:
+        return A.rime_chi2(self.ctx)
+
+    def chi2_async(self, out):
+        A.rime_chi2_async(self.ctx, out)
+        return out
+
+    def ln_norm(self) -> float:
+        return A.rime_ln_norm(self.ctx)
+
+    def sync(self):
+        A.rime_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            A.rime_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

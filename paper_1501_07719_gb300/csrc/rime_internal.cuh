@@ -1,0 +1,176 @@
+// rime_internal.cuh -- types shared by the librime translation units.
+//
+// Data kept on the device by a context (all sizes from rime_dims):
+//   observation   uvw [ntime][na][3] f64, pointing [ntime][na][2] f64,
+//                 data [ntime][nbl][nchan][4] complex, weight [ntime][nbl][nchan]
+//   gains         [ntime][na][nchan][4] complex in the compute precision
+//   channels      per-channel constants of eqs. 2-4 (ChanF / ChanD)
+//   sources       stokes [ntime|1][nsrc] x4, Gaussian quadratic form [nsrc] x4,
+//                 spectral index [nsrc]
+//   delays        per (t, s, a): the geometric delay tau = (u l + v m + w (n-1)) / c
+//                 (double-float pair in FP32 mode, double in FP64 mode) and the
+//                 beam radius rho = |l_s - dl_ta|; [ntime][nsrc][na]
+//   scratch       one FP64 partial chi^2 per thread block, a completion
+//                 counter and a small status block
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rime.h"
+
+namespace rime {
+
+constexpr double kCLight = 299792458.0;
+constexpr double kPi = 3.141592653589793;
+constexpr double kLn2 = 0.6931471805599453;
+// pi^2 / (4 ln 2): the FWHM Gaussian's Fourier-transform constant
+constexpr double kGaussK = kPi * kPi / (4.0 * kLn2);
+constexpr double kLog2e = 1.4426950408889634;
+
+// Error classes: one status word per input class, cleared when that input
+// is set again.
+enum ErrClass { EC_FREQ = 0, EC_UVW = 1, EC_DATA = 2, EC_GAINS = 3, EC_SRC = 4, EC_RUN = 5, EC_N = 8 };
+enum ErrBits : int {
+    EB_NONFINITE = 1,
+    EB_RANGE = 2,       // value outside its domain (l^2+m^2 >= 1, w < 0, nu <= 0, axes)
+};
+
+// Status block in device memory, copied to the host in one transfer.
+struct DevStatus {
+    double chi2;              // result of the fused reduction
+    double aux;               // second scalar (ln-norm)
+    int err[EC_N];            // ErrBits per class
+    long long first_bad[EC_N];
+};
+
+// A unit of work for one thread block: antenna rows [r0, r0+nr) against
+// columns [c0, c0+nc), with the list of thread tiles in tiles[tile0 ..
+// tile0+ntiles). diag = 1 when rows and columns are the same antennas.
+struct Unit {
+    int32_t r0, c0, nr, nc;
+    int32_t tile0, ntiles;
+    int32_t diag, pad;
+};
+// A thread tile: its first row antenna and first column antenna, relative
+// to the unit's r0 / c0.
+struct Tile {
+    uint8_t p, q;
+};
+
+// Per-channel constants, single precision path.
+struct ChanF {
+    float nu_hi, nu_lo;   // nu as a double-float pair (Hz)
+    float hlr;            // 0.5 log2(nu / nu_ref): sqrt of the spectral factor is 2^(alpha hlr)
+    float cnu;            // beam_c * nu[GHz]
+    float nu2;            // nu^2 (Hz^2), for the Gaussian exponent
+    float pad[3];
+};
+// Per-channel constants, double precision path.
+struct ChanD {
+    double nu, hlr, cnu, nu2;
+};
+
+struct rime_ctx_impl;  // forward
+
+// Kernel parameter block for the fused predict / chi^2 kernels.
+struct FusedParams {
+    int na, ntime, nchan, nsrc;
+    long long nbl;
+    int stokes_tstride;        // nsrc*4 if time varying, else 0 (elements)
+    int nchp;                  // channel groups per timestep
+    int nunits;
+    int has_gains, has_weight;
+    const Unit *units;
+    const Tile *tiles;
+    const void *chan;          // ChanF* or ChanD*
+    const double *uvw;         // [ntime][na][3]
+    const float4 *uvw_f;       // [ntime][na] (u, v, w, 0), FP32 path
+    const void *stokes;        // float4* or double4-like (4 x T)
+    const void *gauss;         // 4 x T per source: A, B, C (exponent form), flag
+    const void *alpha;         // T per source
+    const void *tau;           // float2 / double per (t, s, a)
+    const void *rho;           // float / double per (t, s, a)
+    const void *gains;         // complex T [ntime][na][nchan][4]
+    const void *data;          // complex T [ntime][nbl][nchan][4]
+    const void *weight;        // T [ntime][nbl][nchan]
+    void *vis_out;             // complex T [ntime][nbl][nchan][4]
+    double *partials;          // [gridDim] FP64 partial chi^2
+    unsigned int *counter;     // completion counter (reset by the last block)
+    double *result;            // where the last block stores chi^2
+    const DevStatus *status;   // kernels skip their work if any err word is set
+};
+
+// Checks on the status block that every kernel makes before working.
+__device__ __forceinline__ bool inputs_bad(const DevStatus *st) {
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < EC_RUN; i++) e |= st->err[i];
+    return e != 0;
+}
+
+}  // namespace rime
+
+// The opaque context of the public ABI.
+struct rime_ctx {
+    rime_dims dims;
+    long long nbl = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    // observation
+    double *d_freq = nullptr;
+    void *d_chan = nullptr;
+    double *d_uvw = nullptr;
+    void *d_uvw_f = nullptr;          // float4 copy for the FP32 path
+    double *d_pointing = nullptr;
+    void *d_data = nullptr;
+    void *d_weight = nullptr;
+    bool has_data = false, has_weight = false, has_pointing = false;
+    // gains
+    double *d_gains_in = nullptr;     // complex128 staging
+    void *d_gains = nullptr;          // compute precision
+    bool has_gains = false;
+    // sources
+    int nsrc = 0, time_varying = 0;
+    bool sources_set = false;
+    size_t src_cap = 0;               // sources the buffers below can hold
+    size_t src_stokes_rows = 0;       // 1 or ntime
+    double *d_src_in = nullptr;       // copy of the FP64 parameters: lm, stokes, alpha, shape
+    double *src_lm() const { return d_src_in; }
+    double *src_stokes() const { return d_src_in + 2 * src_cap; }
+    double *src_alpha() const { return d_src_in + 2 * src_cap + 4 * src_cap * src_stokes_rows; }
+    double *src_shape() const { return src_alpha() + src_cap; }
+    bool has_shape = false;
+    void *d_stokes = nullptr, *d_gauss = nullptr, *d_alpha = nullptr;
+    void *d_tau = nullptr, *d_rho = nullptr;
+    // work decomposition
+    rime::Unit *d_units = nullptr;
+    rime::Tile *d_tiles = nullptr;
+    int nunits = 0;
+    // scratch
+    double *d_partials = nullptr;
+    size_t partials_cap = 0;
+    unsigned int *d_counter = nullptr;
+    rime::DevStatus *d_status = nullptr;
+    rime::DevStatus *h_status = nullptr;   // pinned
+
+    size_t tsize() const { return dims.precision == RIME_FP64 ? 8 : 4; }
+};
+
+namespace rime {
+// launchers (rime_prep.cu)
+cudaError_t launch_prep_channels(rime_ctx *c);
+cudaError_t launch_validate_uvw(rime_ctx *c);
+cudaError_t launch_validate_data(rime_ctx *c);
+cudaError_t launch_convert_gains(rime_ctx *c);
+cudaError_t launch_prep_sources(rime_ctx *c);
+cudaError_t launch_prep_delays(rime_ctx *c);
+cudaError_t launch_ln_norm(rime_ctx *c);
+// launchers (rime_fused.cu)
+cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2);
+int fused_blocks(const rime_ctx *c);
+}  // namespace rime

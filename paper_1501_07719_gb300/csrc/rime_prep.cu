@@ -1,0 +1,280 @@
+// rime_prep.cu -- upload-time kernels: input checks and the per-channel,
+// per-source and per-(time, source, antenna) factors of eqs. 2-4.
+//
+// Everything the fused kernel needs in double precision is computed here,
+// once per upload, so that the FP32 fused kernel runs no FP64 instruction.
+#include "rime_internal.cuh"
+
+#include <math.h>
+
+namespace rime {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void flag(DevStatus *st, int cls, int bits, long long idx) {
+    atomicOr(&st->err[cls], bits);
+    atomicMin(&st->first_bad[cls], idx);
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+
+// Per-channel constants of eqs. 2-4.
+__global__ void k_prep_channels(int nchan, const double *freq, double ref_freq, double beam_c,
+                                int fp64, void *chan, DevStatus *st) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nchan) return;
+    double nu = freq[k];
+    if (!finite(nu)) flag(st, EC_FREQ, EB_NONFINITE, k);
+    else if (!(nu > 0.0)) flag(st, EC_FREQ, EB_RANGE, k);
+    // sqrt of the spectral factor (nu / nu_ref)^alpha is 2^(alpha * hlr)
+    double hlr = 0.5 * log2(nu / ref_freq);
+    double cnu = beam_c * (nu * 1e-9);
+    if (fp64) {
+        ChanD c{nu, hlr, cnu, nu * nu};
+        reinterpret_cast<ChanD *>(chan)[k] = c;
+    } else {
+        ChanF c;
+        c.nu_hi = (float)nu;
+        c.nu_lo = (float)(nu - (double)c.nu_hi);
+        c.hlr = (float)hlr;
+        c.cnu = (float)cnu;
+        c.nu2 = (float)(nu * nu);
+        c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
+        reinterpret_cast<ChanF *>(chan)[k] = c;
+    }
+}
+
+// uvw / pointing must be finite; the FP32 path also gets a float4 copy of uvw.
+__global__ void k_validate_uvw(long long n_ta, const double *uvw, const double *pointing,
+                               float4 *uvw_f, DevStatus *st) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ta) return;
+    double u = uvw[3 * i], v = uvw[3 * i + 1], w = uvw[3 * i + 2];
+    bool ok = finite(u) && finite(v) && finite(w);
+    if (pointing) ok = ok && finite(pointing[2 * i]) && finite(pointing[2 * i + 1]);
+    if (!ok) flag(st, EC_UVW, EB_NONFINITE, i);
+    if (uvw_f) uvw_f[i] = make_float4((float)u, (float)v, (float)w, 0.f);
+}
+
+template <typename T>
+__global__ void k_validate_data(long long nvis, const T *data, const T *weight, DevStatus *st) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvis) return;
+    bool ok = true;
+    if (data) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) ok = ok && isfinite(data[8 * i + c]);
+    }
+    if (weight) {
+        T w = weight[i];
+        if (!isfinite(w)) ok = false;
+        else if (w < T(0)) flag(st, EC_DATA, EB_RANGE, i);
+    }
+    if (!ok) flag(st, EC_DATA, EB_NONFINITE, i);
+}
+
+// complex128 gains -> compute precision; checks finiteness.
+template <typename T>
+__global__ void k_convert_gains(long long n, const double *in, T *out, DevStatus *st) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;   // n = number of doubles
+    double x = in[i];
+    if (!isfinite(x)) flag(st, EC_GAINS, EB_NONFINITE, i / 8);
+    out[i] = (T)x;
+}
+
+// Per source: checks, the Gaussian exponent's quadratic form, brightness in
+// the compute precision.  Shape factor (the Fourier transform of an
+// elliptical Gaussian with FWHM axes maj, min at position angle pa):
+//   ln g = -K nu^2 / c^2 [maj^2 (du sp + dv cp)^2 + min^2 (du cp - dv sp)^2]
+//        = nu^2 (A du^2 + B du dv + C dv^2),   K = pi^2 / (4 ln 2).
+// The FP32 path stores A, B, C scaled by log2(e) for an exp2.
+template <typename T>
+__global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, const double *stokes,
+                               const double *alpha, const double *shape, T *o_stokes, T *o_gauss,
+                               T *o_alpha, DevStatus *st) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long nst = (long long)stokes_rows * nsrc;
+    if (i < nst) {
+        bool ok = true;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            double x = stokes[4 * i + c];
+            ok = ok && isfinite(x);
+            o_stokes[4 * i + c] = (T)x;
+        }
+        if (!ok) flag(st, EC_SRC, EB_NONFINITE, i % nsrc);
+    }
+    if (i >= nsrc) return;
+    double l = lm[2 * i], m = lm[2 * i + 1], a = alpha[i];
+    double maj = 0.0, mn = 0.0, pa = 0.0;
+    if (shape) {
+        maj = shape[3 * i];
+        mn = shape[3 * i + 1];
+        pa = shape[3 * i + 2];
+    }
+    if (!(isfinite(l) && isfinite(m) && isfinite(a) && isfinite(maj) && isfinite(mn) && isfinite(pa)))
+        flag(st, EC_SRC, EB_NONFINITE, i);
+    else if (!(l * l + m * m < 1.0) || !(mn >= 0.0) || !(maj >= mn))
+        flag(st, EC_SRC, EB_RANGE, i);
+    double sp, cp;
+    sincos(pa, &sp, &cp);
+    double k = -kGaussK / (kCLight * kCLight);
+    if (sizeof(T) == 4) k *= kLog2e;
+    double A = k * (maj * maj * sp * sp + mn * mn * cp * cp);
+    double B = k * 2.0 * sp * cp * (maj * maj - mn * mn);
+    double C = k * (maj * maj * cp * cp + mn * mn * sp * sp);
+    bool gauss = (maj != 0.0 || mn != 0.0);
+    o_gauss[4 * i + 0] = (T)A;
+    o_gauss[4 * i + 1] = (T)B;
+    o_gauss[4 * i + 2] = (T)C;
+    o_gauss[4 * i + 3] = gauss ? T(1) : T(0);
+    o_alpha[i] = (T)a;
+}
+
+// Per (t, s, a): geometric delay tau = (u l + v m + w (n - 1)) / c in
+// seconds (eq. 3 without the frequency), with n - 1 = -(l^2+m^2)/(1+n) (no
+// cancellation), and the beam radius rho = |(l, m) - dl_ta| of eq. 4.
+template <bool FP64>
+__global__ void k_prep_delays(int ntime, int nsrc, int na, const double *uvw, const double *pointing,
+                              const double *lm, void *tau_out, void *rho_out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)ntime * nsrc * na;
+    if (i >= n) return;
+    int a = (int)(i % na);
+    long long ts = i / na;
+    int s = (int)(ts % nsrc);
+    int t = (int)(ts / nsrc);
+    double l = lm[2 * s], m = lm[2 * s + 1];
+    double r2 = l * l + m * m;
+    double n1 = -r2 / (1.0 + sqrt(1.0 - r2));
+    const double *x = uvw + 3 * ((long long)t * na + a);
+    double tau = (x[0] * l + x[1] * m + x[2] * n1) / kCLight;
+    double dl = 0.0, dm = 0.0;
+    if (pointing) {
+        dl = pointing[2 * ((long long)t * na + a)];
+        dm = pointing[2 * ((long long)t * na + a) + 1];
+    }
+    double rho = hypot(l - dl, m - dm);
+    if (FP64) {
+        reinterpret_cast<double *>(tau_out)[i] = tau;
+        reinterpret_cast<double *>(rho_out)[i] = rho;
+    } else {
+        float hi = (float)tau;
+        float lo = (float)(tau - (double)hi);
+        reinterpret_cast<float2 *>(tau_out)[i] = make_float2(hi, lo);
+        reinterpret_cast<float *>(rho_out)[i] = (float)rho;
+    }
+}
+
+// sum ln(2 pi / w) over all visibilities (single block, fixed order).
+template <typename T>
+__global__ void k_ln_norm(long long nvis, const T *weight, DevStatus *st) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (long long i = threadIdx.x; i < nvis; i += blockDim.x) {
+        double w = weight ? (double)weight[i] : 1.0;
+        acc += log(2.0 * 3.141592653589793 / w);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) st->aux = v;
+    }
+}
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+cudaError_t launch_prep_channels(rime_ctx *c) {
+    int n = c->dims.nchan;
+    k_prep_channels<<<blocks_for(n), kThreads, 0, c->stream>>>(
+        n, c->d_freq, c->dims.ref_freq_hz, c->dims.beam_c, c->dims.precision == RIME_FP64, c->d_chan,
+        c->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_uvw(rime_ctx *c) {
+    long long n = (long long)c->dims.ntime * c->dims.na;
+    float4 *uvw_f = c->dims.precision == RIME_FP64 ? nullptr : reinterpret_cast<float4 *>(c->d_uvw_f);
+    k_validate_uvw<<<blocks_for(n), kThreads, 0, c->stream>>>(
+        n, c->d_uvw, c->has_pointing ? c->d_pointing : nullptr, uvw_f, c->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_data(rime_ctx *c) {
+    long long nvis = (long long)c->dims.ntime * c->nbl * c->dims.nchan;
+    if (nvis == 0) return cudaSuccess;
+    if (c->dims.precision == RIME_FP64)
+        k_validate_data<double><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
+            nvis, c->has_data ? (const double *)c->d_data : nullptr,
+            c->has_weight ? (const double *)c->d_weight : nullptr, c->d_status);
+    else
+        k_validate_data<float><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
+            nvis, c->has_data ? (const float *)c->d_data : nullptr,
+            c->has_weight ? (const float *)c->d_weight : nullptr, c->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_gains(rime_ctx *c) {
+    long long n = (long long)c->dims.ntime * c->dims.na * c->dims.nchan * 8;
+    if (c->dims.precision == RIME_FP64)
+        k_convert_gains<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+            n, c->d_gains_in, (double *)c->d_gains, c->d_status);
+    else
+        k_convert_gains<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+            n, c->d_gains_in, (float *)c->d_gains, c->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_sources(rime_ctx *c) {
+    int nsrc = c->nsrc;
+    if (nsrc == 0) return cudaSuccess;
+    int rows = c->time_varying ? c->dims.ntime : 1;
+    long long n = (long long)rows * nsrc;
+    const double *shape = c->has_shape ? c->src_shape() : nullptr;
+    if (c->dims.precision == RIME_FP64)
+        k_prep_sources<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
+            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (double *)c->d_stokes,
+            (double *)c->d_gauss, (double *)c->d_alpha, c->d_status);
+    else
+        k_prep_sources<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
+            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (float *)c->d_stokes,
+            (float *)c->d_gauss, (float *)c->d_alpha, c->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_prep_delays(c);
+}
+
+cudaError_t launch_prep_delays(rime_ctx *c) {
+    int nsrc = c->nsrc;
+    if (nsrc == 0 || !c->sources_set) return cudaSuccess;
+    long long nd = (long long)c->dims.ntime * nsrc * c->dims.na;
+    const double *pt = c->has_pointing ? c->d_pointing : nullptr;
+    if (c->dims.precision == RIME_FP64)
+        k_prep_delays<true><<<blocks_for(nd), kThreads, 0, c->stream>>>(
+            c->dims.ntime, nsrc, c->dims.na, c->d_uvw, pt, c->src_lm(), c->d_tau, c->d_rho);
+    else
+        k_prep_delays<false><<<blocks_for(nd), kThreads, 0, c->stream>>>(
+            c->dims.ntime, nsrc, c->dims.na, c->d_uvw, pt, c->src_lm(), c->d_tau, c->d_rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ln_norm(rime_ctx *c) {
+    long long nvis = (long long)c->dims.ntime * c->nbl * c->dims.nchan;
+    if (c->dims.precision == RIME_FP64)
+        k_ln_norm<double><<<1, 1024, 0, c->stream>>>(
+            nvis, c->has_weight ? (const double *)c->d_weight : nullptr, c->d_status);
+    else
+        k_ln_norm<float><<<1, 1024, 0, c->stream>>>(
+            nvis, c->has_weight ? (const float *)c->d_weight : nullptr, c->d_status);
+    return cudaGetLastError();
+}
+
+}  // namespace rime
