@@ -147,7 +147,7 @@ def test_nonfinite_data_and_negative_weight_are_rejected():
 
 def test_call_order_errors():
     import paper_1501_07719_gb300 as R
-    inp = make_case(rime_synth.custom(5, 2, 2, 2, 0, seed_index=29), "f64")
+    inp = make_case(rime_synth.custom(5, 2, 2, 2, 0, seed_index=29), "f64", gains=False)
     r = R.Rime(inp, R.RIME_FP64)            # no data
     with pytest.raises(R.RimeError) as e:
         r.chi2()
