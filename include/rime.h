@@ -156,6 +156,46 @@ rime_status rime_ln_norm(rime_ctx *ctx, double *ln_norm);
  * status (failed input checks, kernel errors). */
 rime_status rime_sync(rime_ctx *ctx);
 
+/* chi^2 for callers that cannot allocate device memory. The paper has no
+ * counterpart to this call.
+ *
+ * Who needs it: code that runs where cudaMalloc is not available to a
+ * library -- for example inside a host framework whose memory pool has
+ * reserved the device, or in a latency-critical loop where cudaMalloc's
+ * implicit device synchronisation is not acceptable. Every other entry point
+ * allocates device buffers in rime_create / rime_set_*.
+ *
+ * It evaluates the same fused predict + chi^2 as rime_chi2 for one problem
+ * given entirely by the caller, and allocates nothing: all intermediates
+ * (channel constants, converted gains, per-source constants, per-(t, s, a)
+ * delays, work table, per-block partial sums, completion counter, status)
+ * live in one fixed array of 32 MiB declared in the library's device code.
+ * Every GPU on which the library's module containing this call is loaded
+ * holds that array until the process exits.
+ *
+ *   dims, freq_hz, uvw, pointing, data, weight: as for rime_create, but all
+ *             array pointers must be device pointers (pointing and weight may
+ *             be NULL)
+ *   gains     [ntime][na][nchan][4] complex128 device array, or NULL (identity)
+ *   src       the sky model as for rime_set_sources (device pointers)
+ *   chi2_dev  device pointer to one double, receives chi^2
+ *   cuda_stream  the stream to order the work on
+ * Limits: na <= 256, and the problem's intermediates must fit the 32 MiB
+ * array (the 64-antenna, 100-timestep, 64-channel, 200-source FP32 problem
+ * needs about 29 MB); larger problems return RIME_E_INVALID with the size
+ * needed -- use the context API for those.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. Every call reuses the same array and overwrites what the previous
+ * call left there, so calls that overlap on the GPU (concurrent streams, or
+ * several host threads on one device) race: serialise them.
+ * Waits for the stream, then reports input checks like rime_chi2; errors are
+ * read with rime_last_error(NULL). */
+rime_status rime_chi2_noalloc(const rime_dims *dims, const double *freq_hz, const double *uvw,
+                              const double *pointing, const void *data, const void *weight,
+                              const double *gains, const rime_sources *src, double *chi2_dev,
+                              void *cuda_stream);
+
 /* The message for the last failed call on this context ("" if none). */
 const char *rime_last_error(const rime_ctx *ctx);
 

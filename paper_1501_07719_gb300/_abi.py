@@ -60,6 +60,9 @@ def lib():
         L.rime_ln_norm.argtypes = [vp, C.POINTER(C.c_double)]
         L.rime_sync.argtypes = [vp]
         L.rime_destroy.argtypes, L.rime_destroy.restype = [vp], None
+        L.rime_chi2_noalloc.argtypes = [C.POINTER(rime_dims), vp, vp, vp, vp, vp, vp,
+                                        C.POINTER(rime_sources), vp, vp]
+        L.rime_chi2_noalloc.restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async",
                   "rime_ln_norm", "rime_sync"):
@@ -209,3 +212,19 @@ def rime_last_error(ctx) -> str:
 def rime_destroy(ctx):
     if ctx:
         lib().rime_destroy(ctx)
+
+
+def rime_chi2_noalloc(na, ntime, nchan, precision, freq_hz, uvw, pointing, data, weight, gains,
+                      lm, stokes, alpha, shape, chi2_dev, stream=0, ref_freq_hz=1.4e9, beam_c=65.0):
+    """The chi^2 entry point that allocates no device memory (see include/rime.h).
+    Every array argument must be a device tensor; chi2_dev receives the value."""
+    cd, rd = _ctype(precision)
+    k = _Keep()
+    dims = rime_dims(na, ntime, nchan, precision, ref_freq_hz, beam_c)
+    src = make_sources(lm, stokes, alpha, shape, k)
+    s = lib().rime_chi2_noalloc(C.byref(dims), k.ptr(freq_hz, np.float64, "freq_hz"),
+                                k.ptr(uvw, np.float64, "uvw"), k.ptr(pointing, np.float64, "pointing"),
+                                k.ptr(data, cd, "data"), k.ptr(weight, rd, "weight"),
+                                k.ptr(gains, np.complex128, "gains"), C.byref(src),
+                                chi2_dev.data_ptr(), stream or None)
+    _check(s, None)

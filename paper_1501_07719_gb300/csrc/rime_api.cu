@@ -167,6 +167,10 @@ rime_status upload_uvw(rime_ctx *c, const double *uvw, const double *pointing) {
 
 }  // namespace
 
+namespace rime {
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace rime
+
 extern "C" {
 
 int64_t rime_nbl(int32_t na) { return na < 2 ? 0 : (int64_t)na * (na - 1) / 2; }

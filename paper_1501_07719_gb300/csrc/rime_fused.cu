@@ -434,6 +434,47 @@ void build_units(int na, int precision, std::vector<Unit> &units, std::vector<Ti
     else build_units_t<float>(na, units, tiles);
 }
 
+// The same work units as build_units, written into caller-provided arrays
+// (no heap use). Returns the number of units, or -1 if an array is too small.
+template <typename T>
+static int build_units_fixed_t(int na, Unit *units, int max_units, Tile *tiles, int max_tiles, int *ntiles) {
+    using S = Shape<T>;
+    int nu = 0, nt = 0;
+    for (int r0 = 0; r0 < na; r0 += S::ROWS) {
+        int nr = std::min(S::ROWS, na - r0);
+        if (nu >= max_units) return -1;
+        Unit d{r0, r0, nr, nr, nt, 0, 1, 0};
+        for (int pi = 0; pi < nr; pi += S::TP)
+            for (int qj = 0; qj < nr; qj += S::TQ)
+                if (qj + S::TQ - 1 > pi) {
+                    if (nt >= max_tiles) return -1;
+                    tiles[nt++] = Tile{(uint8_t)pi, (uint8_t)qj};
+                }
+        d.ntiles = nt - d.tile0;
+        units[nu++] = d;
+        for (int c0 = r0 + S::ROWS; c0 < na; c0 += S::COLS) {
+            int nc = std::min(S::COLS, na - c0);
+            if (nu >= max_units) return -1;
+            Unit u{r0, c0, nr, nc, nt, 0, 0, 0};
+            for (int pi = 0; pi < nr; pi += S::TP)
+                for (int qj = 0; qj < nc; qj += S::TQ) {
+                    if (nt >= max_tiles) return -1;
+                    tiles[nt++] = Tile{(uint8_t)pi, (uint8_t)qj};
+                }
+            u.ntiles = nt - u.tile0;
+            units[nu++] = u;
+        }
+    }
+    *ntiles = nt;
+    return nu;
+}
+
+int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
+                      int *ntiles) {
+    return precision == RIME_FP64 ? build_units_fixed_t<double>(na, units, max_units, tiles, max_tiles, ntiles)
+                                  : build_units_fixed_t<float>(na, units, max_units, tiles, max_tiles, ntiles);
+}
+
 int fused_blocks(const rime_ctx *c) { return c->dims.ntime * c->dims.nchan * c->nunits; }
 
 template <typename T, bool CHI2, bool WRITE>

@@ -173,4 +173,8 @@ cudaError_t launch_ln_norm(rime_ctx *c);
 // launchers (rime_fused.cu)
 cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2);
 int fused_blocks(const rime_ctx *c);
+int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
+                      int *ntiles);
+// sets the message rime_last_error(NULL) returns (rime_api.cu)
+void set_global_error(const char *msg);
 }  // namespace rime
