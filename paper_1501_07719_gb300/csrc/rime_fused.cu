@@ -1,4 +1,4 @@
-// rime_fused.cu -- the fused RIME predict + chi^2 kernel (eqs. 1-7).
+// rime_fused.cu -- the fused RIME predict + chi^2 kernels (eqs. 1-7).
 //
 // The paper runs three kernels (Sec. 4.2): EK (Algorithm 1) writes the
 // per-antenna factor A_tpsk = E_tpsk K_tpsk to DRAM, B Sum (Algorithm 2)
@@ -6,24 +6,25 @@
 // a tree reduction sums them. Here one kernel does all three:
 //
 //  * a thread block owns one timestep t, one channel k and one "unit" of
-//    antenna pairs (a block of up to 64 row antennas against up to 64
-//    column antennas; na <= 64 is a single unit);
-//  * per chunk of SC sources it stages A = sqrt(f) E K for the unit's
-//    antennas in shared memory (the spectral factor f = (nu/nu_ref)^alpha of
-//    eq. 2 is split as sqrt(f) on each antenna), so every A is computed once
-//    and reused by all ~na/2 baselines that share the antenna;
-//  * each thread accumulates a TP x TQ antenna tile (TP*TQ baselines) with
-//    four complex accumulators per baseline, sum_s z_s X_s for X in
-//    (I, Q, U, V), z = A_p conj(A_q) g;
+//    antenna pairs (up to 64 row antennas against up to 64 (diagonal unit)
+//    or 32 (off-diagonal unit) column antennas; na <= 64 is one unit);
+//  * per chunk of sources it stages the per-antenna factors A = E K in
+//    shared memory, so each is computed once and reused by all ~na/2
+//    baselines that share the antenna; the spectral factor (nu/nu_ref)^alpha
+//    of eq. 2 multiplies the source's Stokes vector instead;
+//  * each thread accumulates a fixed set of baselines with four complex
+//    accumulators per baseline, sum_s z_s X_s for X in (I, Q, U, V),
+//    z = A_p conj(A_q) g (g the Gaussian shape factor, 1 for points);
 //  * the epilogue forms S from the Stokes sums (eq. 2), applies the gains
-//    (eq. 1), and either writes V or forms w |V - D|^2 (eq. 7);
-//  * chi^2: thread -> warp shuffle -> block in FP64 -> one partial per
-//    block; the last block to finish sums the partials in index order, so
-//    the result is deterministic.
+//    (eq. 1) and either writes V or forms w |V - D|^2 (eq. 7);
+//  * chi^2: thread -> warp shuffle -> block (FP64) -> one partial per block;
+//    the last block to finish sums the partials in index order, so the
+//    result is deterministic.
 //
-// FP32 mode keeps the phase exact: nu tau (up to ~1e2 turns) is formed as a
+// FP32 kernel: the phase nu tau (up to ~1e2 turns) is formed as a
 // double-float product and reduced to [-1/2, 1/2] turns without rounding
-// error before sincospi; the FP64 delays come from the upload kernels.
+// error before sincospi; the FP64 delays come from the upload kernels, so the
+// kernel issues no FP64 instruction outside the final reduction.
 #include "rime_internal.cuh"
 
 #include <algorithm>
@@ -31,42 +32,9 @@
 
 namespace rime {
 
-template <typename T>
-struct Shape;
-// FP32: 4x2 antenna tiles, 64-antenna units.
-template <>
-struct Shape<float> {
-    static constexpr int TP = 4;          // row antennas per thread tile
-    static constexpr int TQ = 2;          // column antennas per thread tile
-    static constexpr int NB = TP * TQ;    // baselines per thread
-    static constexpr int ROWS = 64;       // row antennas per unit
-    static constexpr int COLS = 32;       // column antennas per off-diagonal unit
-    static constexpr int THREADS = 288;   // tiles of a 64-antenna diagonal unit (272), whole warps
-    static constexpr int SC = 32;         // sources per staged chunk
-    static constexpr int ASTRIDE = ROWS + 8;
-    static constexpr int MINB = 1;
-};
-// FP64: 2x2 antenna tiles, 32-antenna units (the FP64 accumulators need the registers).
-template <>
-struct Shape<double> {
-    static constexpr int TP = 2;
-    static constexpr int TQ = 2;
-    static constexpr int NB = TP * TQ;
-    static constexpr int ROWS = 32;
-    static constexpr int COLS = 32;
-    static constexpr int THREADS = 256;
-    static constexpr int SC = 16;
-    static constexpr int ASTRIDE = ROWS + 4;
-    static constexpr int MINB = 1;
-};
-
-template <typename T> struct Vec;
-template <> struct Vec<float> { using T2 = float2; using T4 = float4; using Chan = ChanF; };
-template <> struct Vec<double> { using T2 = double2; struct T4 { double x, y, z, w; }; using Chan = ChanD; };
-
-// ---------------------------------------------------------------------------
-// Per-antenna factor A = sqrt(f) E K for one (t, s, a, k)   (eqs. 2-4)
-// ---------------------------------------------------------------------------
+// ===========================================================================
+// Shared device helpers
+// ===========================================================================
 __device__ __forceinline__ float round_int_f(float x) {
     // nearest integer for |x| < 2^22 (1.5 * 2^23 magic constant), ties to even
     const float M = 12582912.0f;
@@ -77,82 +45,111 @@ __device__ __forceinline__ double round_int_d(double x) {
     return __dsub_rn(__dadd_rn(x, M), M);
 }
 
-__device__ __forceinline__ float2 antenna_factor(float2 tau, float rho, float alpha, const ChanF &ch) {
-    // phase nu * tau in turns as a double-float product: nu_hi tau_hi = p + e
-    // exactly, p - round(p) is exact, the small terms add the rest.
-    float p = ch.nu_hi * tau.x;
-    float e = fmaf(ch.nu_hi, tau.x, -p);
-    float r = p - round_int_f(p);
-    float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
-    float sn, cs;
-    sincospif(2.0f * f, &sn, &cs);                 // eq. 3
-    float x = ch.cnu * rho;                        // eq. 4: C nu[GHz] rho
-    float cb = cosf(x);
-    float E = (x < 1.57079632679f) ? cb * cb * cb : 0.0f;
-    float amp = E * exp2f(alpha * ch.hlr);         // sqrt of eq. 2's spectral factor
-    return make_float2(amp * cs, amp * sn);
-}
-
-__device__ __forceinline__ double2 antenna_factor(double tau, double rho, double alpha, const ChanD &ch) {
-    double ph = ch.nu * tau;
-    double r = ph - round_int_d(ph);
-    double sn, cs;
-    sincospi(2.0 * r, &sn, &cs);
-    double x = ch.cnu * rho;
-    double cb = cos(x);
-    double E = (x < 1.5707963267948966) ? cb * cb * cb : 0.0;
-    double amp = E * exp2(alpha * ch.hlr);
-    return make_double2(amp * cs, amp * sn);
-}
-
-__device__ __forceinline__ float gauss_factor(float e) {
+__device__ __forceinline__ float ex2_approx(float e) {
     float g;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
     return g;
 }
-__device__ __forceinline__ double gauss_factor(double e) { return exp(e); }
 
-// ---------------------------------------------------------------------------
-// The kernel
-// ---------------------------------------------------------------------------
-template <typename T>
-struct Smem {
-    using T2 = typename Vec<T>::T2;
-    using T4 = typename Vec<T>::T4;
-    using Chan = typename Vec<T>::Chan;
-    static constexpr int A_ELEMS = 2 * Shape<T>::SC * Shape<T>::ASTRIDE;
-    static constexpr size_t bytes() {
-        return A_ELEMS * sizeof(T2) + Shape<T>::SC * sizeof(T4) * 2 + sizeof(Chan) + 64 * sizeof(double);
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Block-wide deterministic FP64 sum of one value per thread; result valid in
+// thread 0. red: >= 32 doubles of shared memory.
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double x = 0.0;
+    if (warp == 0) {
+        x = lane < THREADS / 32 ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     }
-};
+    return x;
+}
 
-template <typename T, bool CHI2, bool WRITE>
-__global__ void __launch_bounds__(Shape<T>::THREADS, Shape<T>::MINB) k_fused(const FusedParams P) {
-    using S = Shape<T>;
-    using T2 = typename Vec<T>::T2;
-    using T4 = typename Vec<T>::T4;
-    using Chan = typename Vec<T>::Chan;
-    constexpr bool F32 = sizeof(T) == 4;
+// One partial per block, then the last block to arrive sums them in index
+// order and stores the total. All threads of the block must call it.
+template <int THREADS>
+__device__ void finish_chi2(double block_value, const FusedParams &P, double *red, int *sLast) {
+    if (threadIdx.x == 0) {
+        P.partials[blockIdx.x] = block_value;
+        __threadfence();
+        unsigned ticket = atomicAdd(P.counter, 1u);
+        *sLast = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (*sLast) {
+        __threadfence();
+        double s = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) s += __ldcg(&P.partials[i]);
+        double tot = block_sum<THREADS>(s, red);
+        if (threadIdx.x == 0) {
+            *P.result = tot;
+            *P.counter = 0u;
+        }
+    }
+}
 
+// ===========================================================================
+// FP64 kernel: 2 x 2 antenna tiles, 32-antenna units
+// ===========================================================================
+namespace f64 {
+constexpr int TP = 2, TQ = 2, NB = TP * TQ;
+constexpr int ROWS = 32, COLS = 32;
+constexpr int THREADS = 256;
+constexpr int SC = 16;
+constexpr int ASTRIDE = ROWS + 4;
+struct D4 { double x, y, z, w; };
+constexpr size_t smem_bytes() { return 2 * SC * ASTRIDE * sizeof(double2) + 2 * SC * sizeof(D4) + 64 * sizeof(double); }
+
+__device__ __forceinline__ double2 antenna_factor(double tau, double rho, double alpha, const ChanD &ch) {
+    double ph = ch.nu * tau;                 // eq. 3 phase in turns
+    double r = ph - round_int_d(ph);
+    double sn, cs;
+    sincospi(2.0 * r, &sn, &cs);
+    double x = ch.cnu * rho;                 // eq. 4: C nu[GHz] rho
+    double cb = cos(x);
+    double E = (x < 1.5707963267948966) ? cb * cb * cb : 0.0;
+    double amp = E * exp2(alpha * ch.hlr);   // sqrt of eq. 2's spectral factor
+    return make_double2(amp * cs, amp * sn);
+}
+
+template <bool CHI2, bool WRITE>
+__global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2 *sA = reinterpret_cast<T2 *>(smem_raw);                 // [2][SC][ASTRIDE]
-    T4 *sSt = reinterpret_cast<T4 *>(sA + Smem<T>::A_ELEMS);    // [SC] stokes
-    T4 *sGq = sSt + S::SC;                                      // [SC] gauss coeffs * nu^2, flag
-    Chan *sCh = reinterpret_cast<Chan *>(sGq + S::SC);
-    double *sRed = reinterpret_cast<double *>(sCh + 1);          // [32]
+    double2 *sA = reinterpret_cast<double2 *>(smem_raw);            // [2][SC][ASTRIDE]
+    D4 *sSt = reinterpret_cast<D4 *>(sA + 2 * SC * ASTRIDE);         // [SC]
+    D4 *sGq = sSt + SC;                                              // [SC]
+    double *sRed = reinterpret_cast<double *>(sGq + SC);             // [64]
     __shared__ int sLast;
 
     if (inputs_bad(P.status)) return;
-
     const int tid = threadIdx.x;
     const int u = blockIdx.x % P.nunits;
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
     const int t = rest / P.nchan;
     const Unit U = P.units[u];
-    const bool active = tid < U.ntiles;
-
-    if (tid == 0) *sCh = reinterpret_cast<const Chan *>(P.chan)[k];
+    const bool active = tid < U.nbody;
+    const ChanD ch = reinterpret_cast<const ChanD *>(P.chan)[k];
 
     int pl = 0, ql = 0;
     if (active) {
@@ -161,178 +158,129 @@ __global__ void __launch_bounds__(Shape<T>::THREADS, Shape<T>::MINB) k_fused(con
         ql = tl.q;
     }
     const int p0 = U.r0 + pl, q0 = U.c0 + ql;
+    const int pend = U.r0 + U.nr, qend = U.c0 + U.nc;
     unsigned mask = 0;
 #pragma unroll
-    for (int i = 0; i < S::TP; i++)
+    for (int i = 0; i < TP; i++)
 #pragma unroll
-        for (int j = 0; j < S::TQ; j++)
-            if (active && p0 + i < q0 + j && q0 + j < P.na) mask |= 1u << (i * S::TQ + j);
+        for (int j = 0; j < TQ; j++)
+            if (active && p0 + i < pend && q0 + j < qend && p0 + i < q0 + j) mask |= 1u << (i * TQ + j);
 
-    // baseline terms of the Gaussian exponent: du^2, du dv, dv^2 (metres^2)
-    T du2[S::NB], dudv[S::NB], dv2[S::NB];
+    double du2[NB], dudv[NB], dv2[NB];
 #pragma unroll
-    for (int i = 0; i < S::TP; i++) {
+    for (int i = 0; i < TP; i++) {
         int pa = min(p0 + i, P.na - 1);
-        T up, vp;
-        if constexpr (F32) {
-            float4 x = P.uvw_f[(long long)t * P.na + pa];
-            up = x.x; vp = x.y;
-        } else {
-            up = P.uvw[3 * ((long long)t * P.na + pa)];
-            vp = P.uvw[3 * ((long long)t * P.na + pa) + 1];
-        }
+        double up = P.uvw[3 * ((long long)t * P.na + pa)], vp = P.uvw[3 * ((long long)t * P.na + pa) + 1];
 #pragma unroll
-        for (int j = 0; j < S::TQ; j++) {
+        for (int j = 0; j < TQ; j++) {
             int qa = min(q0 + j, P.na - 1);
-            T uq, vq;
-            if constexpr (F32) {
-                float4 x = P.uvw_f[(long long)t * P.na + qa];
-                uq = x.x; vq = x.y;
-            } else {
-                uq = P.uvw[3 * ((long long)t * P.na + qa)];
-                vq = P.uvw[3 * ((long long)t * P.na + qa) + 1];
-            }
-            T du = up - uq, dv = vp - vq;
-            du2[i * S::TQ + j] = du * du;
-            dudv[i * S::TQ + j] = du * dv;
-            dv2[i * S::TQ + j] = dv * dv;
+            double du = up - P.uvw[3 * ((long long)t * P.na + qa)];
+            double dv = vp - P.uvw[3 * ((long long)t * P.na + qa) + 1];
+            du2[i * TQ + j] = du * du;
+            dudv[i * TQ + j] = du * dv;
+            dv2[i * TQ + j] = dv * dv;
         }
     }
 
-    T acc[S::NB][8];
+    double acc[NB][8];
 #pragma unroll
-    for (int b = 0; b < S::NB; b++)
+    for (int b = 0; b < NB; b++)
 #pragma unroll
-        for (int c = 0; c < 8; c++) acc[b][c] = T(0);
+        for (int c = 0; c < 8; c++) acc[b][c] = 0.0;
 
     const int nloc = U.diag ? U.nr : U.nr + U.nc;
-    const T2 *Ar = sA;
-    const T2 *Ac = U.diag ? sA : sA + S::SC * S::ASTRIDE;
-    const T *gauss = reinterpret_cast<const T *>(P.gauss);
-    const T *stokes = reinterpret_cast<const T *>(P.stokes) + (long long)t * P.stokes_tstride;
-    const T *alpha = reinterpret_cast<const T *>(P.alpha);
-    __syncthreads();
-    const Chan ch = *sCh;
+    const double2 *Ar = sA;
+    const double2 *Ac = U.diag ? sA : sA + SC * ASTRIDE;
+    const double *gauss = reinterpret_cast<const double *>(P.gauss);
+    const double *stokes = reinterpret_cast<const double *>(P.stokes) + (long long)t * P.stokes_tstride;
+    const double *alpha = reinterpret_cast<const double *>(P.alpha);
 
-    for (int s0 = 0; s0 < P.nsrc; s0 += S::SC) {
-        const int sc = min(S::SC, P.nsrc - s0);
-        // ---- stage A for the chunk (Algorithm 1, kept on chip) ----
-        for (int j = tid; j < sc * nloc; j += S::THREADS) {
+    for (int s0 = 0; s0 < P.nsrc; s0 += SC) {
+        const int sc = min(SC, P.nsrc - s0);
+        for (int j = tid; j < sc * nloc; j += THREADS) {
             int s = j / nloc, a = j - s * nloc;
             int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
-            T2 *dst = (a < U.nr ? sA + a : sA + S::SC * S::ASTRIDE + (a - U.nr)) + s * S::ASTRIDE;
-            T2 v;
-            {
-                long long di = ((long long)t * P.nsrc + s0 + s) * P.na + ant;
-                if constexpr (F32)
-                    v = antenna_factor(reinterpret_cast<const float2 *>(P.tau)[di],
-                                       reinterpret_cast<const float *>(P.rho)[di], alpha[s0 + s], ch);
-                else
-                    v = antenna_factor(reinterpret_cast<const double *>(P.tau)[di],
-                                       reinterpret_cast<const double *>(P.rho)[di], alpha[s0 + s], ch);
-            }
-            *dst = v;
+            double2 *dst = (a < U.nr ? sA + a : sA + SC * ASTRIDE + (a - U.nr)) + s * ASTRIDE;
+            long long di = ((long long)t * P.nsrc + s0 + s) * P.na + ant;
+            *dst = antenna_factor(reinterpret_cast<const double *>(P.tau)[di],
+                                  reinterpret_cast<const double *>(P.rho)[di], alpha[s0 + s], ch);
         }
-        if (tid < S::SC) {
-            T4 st, gq;
-            if (tid < sc) {
-                const T *x = stokes + 4 * (long long)(s0 + tid);
-                const T *g = gauss + 4 * (long long)(s0 + tid);
-                st.x = x[0]; st.y = x[1]; st.z = x[2]; st.w = x[3];
-                gq.x = g[0] * ch.nu2; gq.y = g[1] * ch.nu2; gq.z = g[2] * ch.nu2; gq.w = g[3];
-            } else {
-                st.x = st.y = st.z = st.w = T(0);
-                gq.x = gq.y = gq.z = gq.w = T(0);
-            }
-            sSt[tid] = st;
-            sGq[tid] = gq;
+        if (tid < sc) {
+            const double *x = stokes + 4 * (long long)(s0 + tid);
+            const double *g = gauss + 4 * (long long)(s0 + tid);
+            sSt[tid] = D4{x[0], x[1], x[2], x[3]};
+            sGq[tid] = D4{g[0] * ch.nu2, g[1] * ch.nu2, g[2] * ch.nu2, g[3]};
         }
         __syncthreads();
-        // ---- source sum for this thread's baselines (Algorithm 2) ----
         if (active) {
-#pragma unroll 2
             for (int s = 0; s < sc; s++) {
-                const T4 st = sSt[s];
-                const T4 gq = sGq[s];
-                T2 ap[S::TP], aq[S::TQ];
+                const D4 st = sSt[s];
+                const D4 gq = sGq[s];
+                double2 ap[TP], aq[TQ];
 #pragma unroll
-                for (int i = 0; i < S::TP; i++) ap[i] = Ar[s * S::ASTRIDE + pl + i];
+                for (int i = 0; i < TP; i++) ap[i] = Ar[s * ASTRIDE + pl + i];
 #pragma unroll
-                for (int j = 0; j < S::TQ; j++) aq[j] = Ac[s * S::ASTRIDE + ql + j];
-                const bool is_gauss = gq.w != T(0);
+                for (int j = 0; j < TQ; j++) aq[j] = Ac[s * ASTRIDE + ql + j];
+                const bool is_gauss = gq.w != 0.0;
 #pragma unroll
-                for (int i = 0; i < S::TP; i++)
+                for (int i = 0; i < TP; i++)
 #pragma unroll
-                    for (int j = 0; j < S::TQ; j++) {
-                        const int b = i * S::TQ + j;
-                        // z = A_p conj(A_q)
-                        T zr = ap[i].x * aq[j].x + ap[i].y * aq[j].y;
-                        T zi = ap[i].y * aq[j].x - ap[i].x * aq[j].y;
+                    for (int j = 0; j < TQ; j++) {
+                        const int b = i * TQ + j;
+                        double zr = ap[i].x * aq[j].x + ap[i].y * aq[j].y;
+                        double zi = ap[i].y * aq[j].x - ap[i].x * aq[j].y;
                         if (is_gauss) {
-                            T g = gauss_factor(gq.x * du2[b] + gq.y * dudv[b] + gq.z * dv2[b]);
+                            double g = exp(gq.x * du2[b] + gq.y * dudv[b] + gq.z * dv2[b]);
                             zr *= g;
                             zi *= g;
                         }
-                        acc[b][0] += zr * st.x; acc[b][1] += zi * st.x;   // I
-                        acc[b][2] += zr * st.y; acc[b][3] += zi * st.y;   // Q
-                        acc[b][4] += zr * st.z; acc[b][5] += zi * st.z;   // U
-                        acc[b][6] += zr * st.w; acc[b][7] += zi * st.w;   // V
+                        acc[b][0] += zr * st.x; acc[b][1] += zi * st.x;
+                        acc[b][2] += zr * st.y; acc[b][3] += zi * st.y;
+                        acc[b][4] += zr * st.z; acc[b][5] += zi * st.z;
+                        acc[b][6] += zr * st.w; acc[b][7] += zi * st.w;
                     }
             }
         }
         __syncthreads();
     }
 
-    // ---- epilogue: S (eq. 2), gains (eq. 1), chi^2 terms (eq. 7) ----
-    T chi = T(0);
-    const T2 *gains = reinterpret_cast<const T2 *>(P.gains);
-    const T2 *data = reinterpret_cast<const T2 *>(P.data);
-    const T *weight = reinterpret_cast<const T *>(P.weight);
-    T2 *vis = reinterpret_cast<T2 *>(P.vis_out);
+    double chi = 0.0;
+    const double2 *gains = reinterpret_cast<const double2 *>(P.gains);
+    const double2 *data = reinterpret_cast<const double2 *>(P.data);
+    const double *weight = reinterpret_cast<const double *>(P.weight);
+    double2 *vis = reinterpret_cast<double2 *>(P.vis_out);
 #pragma unroll
-    for (int i = 0; i < S::TP; i++) {
-        const int p = p0 + i;
-        T2 gp[4];
-        if (P.has_gains && (mask >> (i * S::TQ)) & ((1u << S::TQ) - 1)) {
-            const T2 *g = gains + 4 * (((long long)t * P.na + p) * P.nchan + k);
+    for (int i = 0; i < TP; i++)
 #pragma unroll
-            for (int c = 0; c < 4; c++) gp[c] = g[c];
-        }
-#pragma unroll
-        for (int j = 0; j < S::TQ; j++) {
-            const int b = i * S::TQ + j;
+        for (int j = 0; j < TQ; j++) {
+            const int b = i * TQ + j;
             if (!((mask >> b) & 1u)) continue;
-            const int q = q0 + j;
-            // S from the Stokes sums: [[I+Q, U+iV], [U-iV, I-Q]]
-            T2 Sm[4];
-            Sm[0].x = acc[b][0] + acc[b][2]; Sm[0].y = acc[b][1] + acc[b][3];
-            Sm[1].x = acc[b][4] - acc[b][7]; Sm[1].y = acc[b][5] + acc[b][6];
-            Sm[2].x = acc[b][4] + acc[b][7]; Sm[2].y = acc[b][5] - acc[b][6];
-            Sm[3].x = acc[b][0] - acc[b][2]; Sm[3].y = acc[b][1] - acc[b][3];
-            T2 V[4];
+            const int p = p0 + i, q = q0 + j;
+            double2 Sm[4];
+            Sm[0] = make_double2(acc[b][0] + acc[b][2], acc[b][1] + acc[b][3]);   // I + Q
+            Sm[1] = make_double2(acc[b][4] - acc[b][7], acc[b][5] + acc[b][6]);   // U + iV
+            Sm[2] = make_double2(acc[b][4] + acc[b][7], acc[b][5] - acc[b][6]);   // U - iV
+            Sm[3] = make_double2(acc[b][0] - acc[b][2], acc[b][1] - acc[b][3]);   // I - Q
+            double2 V[4];
             if (P.has_gains) {
-                const T2 *gq_ = gains + 4 * (((long long)t * P.na + q) * P.nchan + k);
-                T2 gq[4];
-#pragma unroll
-                for (int c = 0; c < 4; c++) gq[c] = gq_[c];
-                // X = G_p S
-                T2 X[4];
+                const double2 *gp = gains + 4 * (((long long)t * P.na + p) * P.nchan + k);
+                const double2 *gq = gains + 4 * (((long long)t * P.na + q) * P.nchan + k);
+                double2 X[4];
 #pragma unroll
                 for (int r = 0; r < 2; r++)
 #pragma unroll
-                    for (int cc = 0; cc < 2; cc++) {
-                        T2 a = gp[2 * r], bb = gp[2 * r + 1], s0v = Sm[cc], s1v = Sm[2 + cc];
-                        X[2 * r + cc].x = a.x * s0v.x - a.y * s0v.y + bb.x * s1v.x - bb.y * s1v.y;
-                        X[2 * r + cc].y = a.x * s0v.y + a.y * s0v.x + bb.x * s1v.y + bb.y * s1v.x;
+                    for (int c = 0; c < 2; c++) {
+                        double2 a = gp[2 * r], bb = gp[2 * r + 1], s0v = Sm[c], s1v = Sm[2 + c];
+                        X[2 * r + c] = make_double2(a.x * s0v.x - a.y * s0v.y + bb.x * s1v.x - bb.y * s1v.y,
+                                                    a.x * s0v.y + a.y * s0v.x + bb.x * s1v.y + bb.y * s1v.x);
                     }
-                // V = X G_q^H : V_rc = sum_m X_rm conj(Gq_cm)
 #pragma unroll
                 for (int r = 0; r < 2; r++)
 #pragma unroll
-                    for (int cc = 0; cc < 2; cc++) {
-                        T2 x0 = X[2 * r], x1 = X[2 * r + 1], g0 = gq[2 * cc], g1 = gq[2 * cc + 1];
-                        V[2 * r + cc].x = x0.x * g0.x + x0.y * g0.y + x1.x * g1.x + x1.y * g1.y;
-                        V[2 * r + cc].y = x0.y * g0.x - x0.x * g0.y + x1.y * g1.x - x1.x * g1.y;
+                    for (int c = 0; c < 2; c++) {
+                        double2 x0 = X[2 * r], x1 = X[2 * r + 1], g0 = gq[2 * c], g1 = gq[2 * c + 1];
+                        V[2 * r + c] = make_double2(x0.x * g0.x + x0.y * g0.y + x1.x * g1.x + x1.y * g1.y,
+                                                    x0.y * g0.x - x0.x * g0.y + x1.y * g1.x - x1.x * g1.y);
                     }
             } else {
 #pragma unroll
@@ -345,147 +293,532 @@ __global__ void __launch_bounds__(Shape<T>::THREADS, Shape<T>::MINB) k_fused(con
                 for (int c = 0; c < 4; c++) vis[4 * row + c] = V[c];
             }
             if constexpr (CHI2) {
-                T r2 = T(0);
+                double r2 = 0.0;
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    T2 d = data[4 * row + c];
-                    T dr = V[c].x - d.x, di = V[c].y - d.y;
+                    double2 d = data[4 * row + c];
+                    double dr = V[c].x - d.x, di = V[c].y - d.y;
                     r2 += dr * dr + di * di;
                 }
-                chi += (P.has_weight ? weight[row] : T(1)) * r2;
+                chi += (P.has_weight ? weight[row] : 1.0) * r2;
             }
         }
-    }
-
     if constexpr (CHI2) {
-        const int lane = tid & 31, warp = tid >> 5;
-        T v = chi;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sRed[warp] = (double)v;
-        __syncthreads();
-        if (warp == 0) {
-            double x = lane < S::THREADS / 32 ? sRed[lane] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) {
-                P.partials[blockIdx.x] = x;
-                __threadfence();
-                unsigned ticket = atomicAdd(P.counter, 1u);
-                sLast = (ticket == gridDim.x - 1);
-            }
-        }
-        __syncthreads();
-        if (sLast) {
-            __threadfence();
-            double s = 0.0;
-            for (int i = tid; i < (int)gridDim.x; i += S::THREADS) s += __ldcg(&P.partials[i]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            __syncthreads();
-            if (lane == 0) sRed[warp] = s;
-            __syncthreads();
-            if (warp == 0) {
-                double x = lane < S::THREADS / 32 ? sRed[lane] : 0.0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                if (lane == 0) {
-                    *P.result = x;
-                    *P.counter = 0u;
-                }
-            }
-        }
+        double bsum = block_sum<THREADS>(chi, sRed);
+        finish_chi2<THREADS>(bsum, P, sRed, &sLast);
+    }
+}
+}  // namespace f64
+
+// ===========================================================================
+// FP32 kernel: 1 x 8 antenna tiles, 256 threads, 2 blocks per SM
+// ===========================================================================
+namespace f32 {
+#ifndef RIME_F32_MIN_BLOCKS
+#define RIME_F32_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
+#endif
+constexpr int THREADS = 256;
+constexpr int SC = 16;               // sources per chunk
+constexpr int ROWS = 64, COLS = 32;  // unit shape (off-diagonal: 64 x 32)
+constexpr int NLOC = ROWS + COLS;    // antennas staged per unit, at most
+constexpr int RSTR = 96;             // staged row of a per-antenna quantity: 64 antennas, 4 pad per 8
+constexpr int CSTR = 48;             // the same for the 32 column antennas of off-diagonal units
+constexpr int NSLOT = 8;             // baselines per thread
+
+// padded position of antenna a in a staged row of floats: 8 antennas per 12
+// floats, so 8-antenna groups start 16-byte aligned in distinct bank groups
+__device__ __forceinline__ int apad(int a) { return a + ((a >> 3) << 2); }
+
+// The source sum runs on packed pairs of FP32 values (two FMAs per
+// instruction) over pairs of adjacent baseline slots: the per-antenna
+// factors are staged as separate real and imaginary rows, so the column
+// factors of slots j and j+1 are one 8-byte pair.
+//
+// The Gaussian exponent of baseline (p, q) for source s is the quadratic form
+// Qf(x_p - x_q) of the antenna coordinates x = (u, v); it is evaluated as
+// Qf(x_p) + Qf(x_q) - x_p . L(x_q) with L(x) = grad Qf(x), from per-antenna
+// values staged with the factors.
+struct Smem {
+    float Kx[SC * RSTR], Ky[SC * RSTR];            // staged A = x + iy, row antennas
+    float Cx[SC * CSTR], Cy[SC * CSTR];            // column antennas (off-diagonal units)
+    float Qr[SC * RSTR], Lxr[SC * RSTR], Lyr[SC * RSTR];   // Gaussian form, row antennas
+    float Qc[SC * CSTR], Lxc[SC * CSTR], Lyc[SC * CSTR];   // Gaussian form, columns
+    float2 rTau[SC * NLOC];     // prefetched delays (hi, lo) of the next chunk
+    float rRho[SC * NLOC];      // prefetched beam radii
+    float4 rSt[SC];             // prefetched Stokes
+    float4 rG[SC];              // prefetched Gaussian coefficients
+    float rAl[SC];              // prefetched spectral indices
+    float4 St[SC][2];           // (I, I, Q, Q), (U, U, V, V), scaled (see staging)
+    float Gf[SC];               // 1 for a Gaussian source
+    float2 uv[NLOC];            // antenna (u, v) at this timestep, unit order
+    double red[32];
+};
+
+// Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
+// nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small
+// products add the rest; the result is reduced to about [-1/2, 1/2] turns.
+__device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
+    float p = ch.nu_hi * tau.x;
+    float e = fmaf(ch.nu_hi, tau.x, -p);
+    float r = p - round_int_f(p);
+    float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
+    float sn, cs;
+    sincospif(2.0f * f, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+// Beam E = cos^3(C nu[GHz] rho) (eq. 4), zero past the first null.
+__device__ __forceinline__ float beam(float rho, const ChanF &ch) {
+    float x = ch.cnu * rho;
+    float cb = cosf(x);
+    return (x < 1.57079632679f) ? cb * cb * cb : 0.0f;
+}
+
+// Local (row, column) antennas of slot j of a thread tile; rev = 1 when the
+// tile forms the pair in the order (column, row) and the accumulated sums
+// must be conjugated. Body tile: row p, columns q .. q+7. Head tile: with
+// x_i = b0 + ((fold + i) mod 8), slots 0..3 pair x_0 with x_1..x_4 and slots
+// 4..6 pair x_4 with x_5..x_7; slot 7 is unused.
+__device__ __forceinline__ void slot_pair(const Tile &tl, int role, int j, int &p, int &q, bool &rev) {
+    if (role == 2) {
+        const int b0 = tl.p, r = tl.fold;
+        const int a = j < 4 ? 0 : 4;
+        const int xa = b0 + ((r + a) & 7), xb = b0 + ((r + j + 1) & 7);
+        rev = xa > xb;
+        p = rev ? xb : xa;
+        q = rev ? xa : xb;
+    } else {
+        p = tl.p;
+        q = tl.q + j;
+        rev = false;
     }
 }
 
-// ---------------------------------------------------------------------------
-// Host side: work units and launch
-// ---------------------------------------------------------------------------
-template <typename T>
-static void build_units_t(int na, std::vector<Unit> &units, std::vector<Tile> &tiles) {
-    using S = Shape<T>;
-    units.clear();
-    tiles.clear();
-    for (int r0 = 0; r0 < na; r0 += S::ROWS) {
-        int nr = std::min(S::ROWS, na - r0);
-        // diagonal unit: tiles with at least one pair p < q
-        {
-            Unit u{r0, r0, nr, nr, (int)tiles.size(), 0, 1, 0};
-            for (int pi = 0; pi < nr; pi += S::TP)
-                for (int qj = 0; qj < nr; qj += S::TQ)
-                    if (qj + S::TQ - 1 > pi) tiles.push_back(Tile{(uint8_t)pi, (uint8_t)qj});
-            u.ntiles = (int)tiles.size() - u.tile0;
-            units.push_back(u);
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Two slots: z = a conj(b) for rows (ax, ay) (as pairs over the two slots)
+// and columns (bx, by), optionally times the Gaussian factors, accumulated
+// against (I, Q, U, V): acc[X][0] holds the real parts of the two slots,
+// acc[X][1] the imaginary parts.
+struct Pair {
+    float2 re[4], im[4];
+};
+__device__ __forceinline__ void accumulate2(Pair &acc, float2 ax, float2 ay, float2 bx, float2 by,
+                                            const float4 &s01, const float4 &s23) {
+    const float2 zr = __ffma2_rn(ax, bx, __fmul2_rn(ay, by));
+    const float2 zi = __ffma2_rn(ay, bx, __fmul2_rn(f2(-ax.x, -ax.y), by));
+    const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        acc.re[c] = __ffma2_rn(zr, X[c], acc.re[c]);
+        acc.im[c] = __ffma2_rn(zi, X[c], acc.im[c]);
+    }
+}
+__device__ __forceinline__ void accumulate2g(Pair &acc, float2 ax, float2 ay, float2 bx, float2 by, float2 g,
+                                             const float4 &s01, const float4 &s23) {
+    const float2 zr = __fmul2_rn(__ffma2_rn(ax, bx, __fmul2_rn(ay, by)), g);
+    const float2 zi = __fmul2_rn(__ffma2_rn(ay, bx, __fmul2_rn(f2(-ax.x, -ax.y), by)), g);
+    const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        acc.re[c] = __ffma2_rn(zr, X[c], acc.re[c]);
+        acc.im[c] = __ffma2_rn(zi, X[c], acc.im[c]);
+    }
+}
+// Gaussian factors of two slots: 2^(Qf(x_p) + Qf(x_q) - x_p . L(x_q)), log2 units
+__device__ __forceinline__ float2 gauss2(float2 qp, float2 up, float2 vp, float2 qq, float2 lx, float2 ly) {
+    const float2 e = __ffma2_rn(f2(-up.x, -up.y), lx, __ffma2_rn(f2(-vp.x, -vp.y), ly, __fadd2_rn(qp, qq)));
+    return f2(ex2_approx(e.x), ex2_approx(e.y));
+}
+
+template <bool CHI2, bool WRITE>
+__global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int sLast;
+
+    if (inputs_bad(P.status)) return;
+    const int tid = threadIdx.x;
+    const int u = blockIdx.x % P.nunits;
+    const int rest = blockIdx.x / P.nunits;
+    const int k = rest % P.nchan;
+    const int t = rest / P.nchan;
+    const Unit U = P.units[u];
+    const ChanF ch = reinterpret_cast<const ChanF *>(P.chan)[k];
+    const int nloc = U.diag ? U.nr : U.nr + U.nc;
+    // this thread's items (s, a) of a chunk: start and stride in (s, a)
+    const int it_s0 = tid / nloc, it_a0 = tid - (tid / nloc) * nloc;
+    const int it_ds = THREADS / nloc, it_da = THREADS - (THREADS / nloc) * nloc;
+    const float2 *tau = reinterpret_cast<const float2 *>(P.tau);
+    const float *rho = reinterpret_cast<const float *>(P.rho);
+    const float *stokes = reinterpret_cast<const float *>(P.stokes) + (long long)t * P.stokes_tstride;
+    const float *gauss = reinterpret_cast<const float *>(P.gauss);
+    const float *alpha = reinterpret_cast<const float *>(P.alpha);
+
+    // prefetch of one chunk's per-(s, a) delays and per-source constants
+    auto issue = [&](int s0) {
+        const int sc = min(SC, P.nsrc - s0);
+        for (int s = it_s0, a = it_a0; s < sc;) {
+            int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+            long long di = ((long long)t * P.nsrc + s0 + s) * P.na + ant;
+            cp_async8(&S.rTau[s * NLOC + a], tau + di);
+            cp_async4(&S.rRho[s * NLOC + a], rho + di);
+            a += it_da;
+            s += it_ds;
+            if (a >= nloc) { a -= nloc; s += 1; }
         }
-        // off-diagonal units: all pairs valid
-        for (int c0 = r0 + S::ROWS; c0 < na; c0 += S::COLS) {
-            int nc = std::min(S::COLS, na - c0);
-            Unit u{r0, c0, nr, nc, (int)tiles.size(), 0, 0, 0};
-            for (int pi = 0; pi < nr; pi += S::TP)
-                for (int qj = 0; qj < nc; qj += S::TQ) tiles.push_back(Tile{(uint8_t)pi, (uint8_t)qj});
-            u.ntiles = (int)tiles.size() - u.tile0;
-            units.push_back(u);
+        if (tid < sc) {
+            cp_async16(&S.rSt[tid], stokes + 4 * (long long)(s0 + tid));
+            cp_async16(&S.rG[tid], gauss + 4 * (long long)(s0 + tid));
+            cp_async4(&S.rAl[tid], alpha + s0 + tid);
+        }
+        cp_async_commit();
+    };
+    if (P.nsrc > 0) issue(0);
+    for (int a = tid; a < nloc; a += THREADS) {
+        int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+        float4 x = P.uvw_f[(long long)t * P.na + ant];
+        S.uv[a] = f2(x.x, x.y);
+    }
+
+    // ---- this thread's 8 baselines ----
+    const int hbase = (U.nbody + 31) & ~31;
+    int role = 0;   // 0 idle, 1 body, 2 head
+    Tile tl{0, 0, 0, 0};
+    if (tid < U.nbody) {
+        role = 1;
+        tl = P.tiles[U.tile0 + tid];
+    } else if (tid >= hbase && tid - hbase < U.nhead) {
+        role = 2;
+        tl = P.tiles[U.tile0 + U.nbody + (tid - hbase)];
+    }
+    const int qlim = U.diag ? U.nr : U.nc;
+    unsigned mask = 0;
+#pragma unroll
+    for (int j = 0; j < NSLOT; j++) {
+        int pj, qj;
+        bool rev;
+        slot_pair(tl, role, j, pj, qj, rev);
+        bool ok = role != 0 && pj < U.nr && qj < qlim && U.r0 + pj < U.c0 + qj;
+        if (role == 2 && j == 7) ok = false;
+        if (ok) mask |= 1u << j;
+    }
+    const float *KxC = U.diag ? S.Kx : S.Cx;
+    const float *KyC = U.diag ? S.Ky : S.Cy;
+    const float *QC = U.diag ? S.Qr : S.Qc;
+    const float *LxC = U.diag ? S.Lxr : S.Lxc;
+    const float *LyC = U.diag ? S.Lyr : S.Lyc;
+    const int cstr = U.diag ? RSTR : CSTR;
+    const bool pointing = P.has_pointing != 0;
+
+    Pair acc[NSLOT / 2];
+#pragma unroll
+    for (int h = 0; h < NSLOT / 2; h++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
+
+    for (int s0 = 0; s0 < P.nsrc; s0 += SC) {
+        const int sc = min(SC, P.nsrc - s0);
+        cp_async_wait_all();
+        __syncthreads();
+        // ---- stage the per-antenna factors of the chunk (Algorithm 1) ----
+        // With pointing errors A = E K per antenna; without, every antenna sees
+        // the same beam E_s and A = K, the E_s^2 of the baseline going into the
+        // source's Stokes scale below.
+        for (int s = it_s0, a = it_a0; s < sc;) {
+            float2 v = phase_factor(S.rTau[s * NLOC + a], ch);
+            if (pointing) {
+                float E = beam(S.rRho[s * NLOC + a], ch);
+                v.x *= E;
+                v.y *= E;
+            }
+            const float4 g = S.rG[s];
+            const float2 xa = S.uv[a];
+            // Gaussian form (log2 units, times nu^2): Qf(x), grad Qf(x)
+            const float A = g.x * ch.nu2, B = g.y * ch.nu2, C = g.z * ch.nu2;
+            const float q = xa.x * fmaf(A, xa.x, B * xa.y) + C * xa.y * xa.y;
+            const float lx = fmaf(2.f * A, xa.x, B * xa.y), ly = fmaf(B, xa.x, 2.f * C * xa.y);
+            if (a < U.nr) {
+                const int o = s * RSTR + apad(a);
+                S.Kx[o] = v.x; S.Ky[o] = v.y; S.Qr[o] = q; S.Lxr[o] = lx; S.Lyr[o] = ly;
+            } else {
+                const int o = s * CSTR + apad(a - U.nr);
+                S.Cx[o] = v.x; S.Cy[o] = v.y; S.Qc[o] = q; S.Lxc[o] = lx; S.Lyc[o] = ly;
+            }
+            a += it_da;
+            s += it_ds;
+            if (a >= nloc) { a -= nloc; s += 1; }
+        }
+        if (tid < sc) {
+            // spectral factor (nu / nu_ref)^alpha = 2^(2 alpha hlr) of eq. 2
+            float f = exp2f(2.0f * S.rAl[tid] * ch.hlr);
+            if (!pointing) {
+                float E = beam(S.rRho[tid * NLOC], ch);
+                f *= E * E;
+            }
+            float4 st = S.rSt[tid];
+            S.St[tid][0] = make_float4(st.x * f, st.x * f, st.y * f, st.y * f);
+            S.St[tid][1] = make_float4(st.z * f, st.z * f, st.w * f, st.w * f);
+            S.Gf[tid] = S.rG[tid].w;
+        }
+        __syncthreads();
+        if (s0 + SC < P.nsrc) issue(s0 + SC);
+
+        // ---- source sum for this thread's baselines (Algorithm 2) ----
+        if (role == 1) {
+            const int ip = apad(tl.p), iq = apad(tl.q);
+            const float2 uvp = S.uv[tl.p];
+            const float2 up = f2(uvp.x, uvp.x), vp = f2(uvp.y, uvp.y);
+#pragma unroll 1
+            for (int s = 0; s < sc; s++) {
+                const float4 s01 = S.St[s][0], s23 = S.St[s][1];
+                const float axs = S.Kx[s * RSTR + ip], ays = S.Ky[s * RSTR + ip];
+                const float2 ax = f2(axs, axs), ay = f2(ays, ays);
+                const float4 *bxv = reinterpret_cast<const float4 *>(KxC + s * cstr + iq);
+                const float4 *byv = reinterpret_cast<const float4 *>(KyC + s * cstr + iq);
+                const float4 bx01 = bxv[0], bx23 = bxv[1], by01 = byv[0], by23 = byv[1];
+                const float2 bx[4] = {f2(bx01.x, bx01.y), f2(bx01.z, bx01.w), f2(bx23.x, bx23.y), f2(bx23.z, bx23.w)};
+                const float2 by[4] = {f2(by01.x, by01.y), f2(by01.z, by01.w), f2(by23.x, by23.y), f2(by23.z, by23.w)};
+                if (S.Gf[s] != 0.f) {
+                    const float qps = S.Qr[s * RSTR + ip];
+                    const float2 qp = f2(qps, qps);
+                    const float4 *qv = reinterpret_cast<const float4 *>(QC + s * cstr + iq);
+                    const float4 *lxv = reinterpret_cast<const float4 *>(LxC + s * cstr + iq);
+                    const float4 *lyv = reinterpret_cast<const float4 *>(LyC + s * cstr + iq);
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const float4 q4 = qv[h], lx4 = lxv[h], ly4 = lyv[h];
+                        const float2 g0 = gauss2(qp, up, vp, f2(q4.x, q4.y), f2(lx4.x, lx4.y), f2(ly4.x, ly4.y));
+                        const float2 g1 = gauss2(qp, up, vp, f2(q4.z, q4.w), f2(lx4.z, lx4.w), f2(ly4.z, ly4.w));
+                        accumulate2g(acc[2 * h], ax, ay, bx[2 * h], by[2 * h], g0, s01, s23);
+                        accumulate2g(acc[2 * h + 1], ax, ay, bx[2 * h + 1], by[2 * h + 1], g1, s01, s23);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < 4; h++) accumulate2(acc[h], ax, ay, bx[h], by[h], s01, s23);
+                }
+            }
+        } else if (role == 2) {
+            const int hb = apad(tl.p), r = tl.fold;
+            int ho[8];   // shared-memory offsets of x_0..x_7 (one 8-antenna block)
+#pragma unroll
+            for (int i = 0; i < 8; i++) ho[i] = hb + ((r + i) & 7);
+            const float2 uv0 = S.uv[tl.p + (r & 7)], uv4 = S.uv[tl.p + ((r + 4) & 7)];
+            // rows of the four slot pairs: (x0, x0), (x0, x0), (x4, x4), (x4, x4)
+            const float2 up[2] = {f2(uv0.x, uv0.x), f2(uv4.x, uv4.x)};
+            const float2 vp[2] = {f2(uv0.y, uv0.y), f2(uv4.y, uv4.y)};
+#pragma unroll 1
+            for (int s = 0; s < sc; s++) {
+                const float4 s01 = S.St[s][0], s23 = S.St[s][1];
+                const float *kx = S.Kx + s * RSTR, *ky = S.Ky + s * RSTR;
+                const float2 ax[2] = {f2(kx[ho[0]], kx[ho[0]]), f2(kx[ho[4]], kx[ho[4]])};
+                const float2 ay[2] = {f2(ky[ho[0]], ky[ho[0]]), f2(ky[ho[4]], ky[ho[4]])};
+                const bool is_gauss = S.Gf[s] != 0.f;
+                const float *qq = S.Qr + s * RSTR, *lx = S.Lxr + s * RSTR, *ly = S.Lyr + s * RSTR;
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const int r2 = h < 2 ? 0 : 1;
+                    const int c0 = ho[2 * h + 1], c1 = h < 3 ? ho[2 * h + 2] : ho[0];   // slot 7 unused
+                    const float2 bx = f2(kx[c0], kx[c1]), by = f2(ky[c0], ky[c1]);
+                    if (is_gauss) {
+                        const float qps = qq[ho[4 * r2]];
+                        const float2 g = gauss2(f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]),
+                                                f2(lx[c0], lx[c1]), f2(ly[c0], ly[c1]));
+                        accumulate2g(acc[h], ax[r2], ay[r2], bx, by, g, s01, s23);
+                    } else {
+                        accumulate2(acc[h], ax[r2], ay[r2], bx, by, s01, s23);
+                    }
+                }
+            }
         }
     }
+
+    // ---- epilogue: S (eq. 2), gains (eq. 1), chi^2 terms (eq. 7) ----
+    float chi = 0.f;
+    const float2 *gains = reinterpret_cast<const float2 *>(P.gains);
+    const float2 *data = reinterpret_cast<const float2 *>(P.data);
+    const float *weight = reinterpret_cast<const float *>(P.weight);
+    float2 *vis = reinterpret_cast<float2 *>(P.vis_out);
+#pragma unroll
+    for (int j = 0; j < NSLOT; j++) {
+        if (!((mask >> j) & 1u)) continue;
+        int pj, qj;
+        bool rev;
+        slot_pair(tl, role, j, pj, qj, rev);
+        const int p = U.r0 + pj, q = U.c0 + qj;
+        const Pair &a = acc[j >> 1];
+        const bool hi = j & 1;
+        // the sums of z for the reversed pair are the conjugates
+        const float cj = rev ? -1.f : 1.f;
+        const float Ir = hi ? a.re[0].y : a.re[0].x, Ii = cj * (hi ? a.im[0].y : a.im[0].x);
+        const float Qr = hi ? a.re[1].y : a.re[1].x, Qi = cj * (hi ? a.im[1].y : a.im[1].x);
+        const float Ur = hi ? a.re[2].y : a.re[2].x, Ui = cj * (hi ? a.im[2].y : a.im[2].x);
+        const float Vr = hi ? a.re[3].y : a.re[3].x, Vi = cj * (hi ? a.im[3].y : a.im[3].x);
+        float2 Sm[4];
+        Sm[0] = make_float2(Ir + Qr, Ii + Qi);   // I + Q
+        Sm[1] = make_float2(Ur - Vi, Ui + Vr);   // U + iV
+        Sm[2] = make_float2(Ur + Vi, Ui - Vr);   // U - iV
+        Sm[3] = make_float2(Ir - Qr, Ii - Qi);   // I - Q
+        float2 V[4];
+        if (P.has_gains) {
+            const float4 *gp4 = reinterpret_cast<const float4 *>(gains + 4 * (((long long)t * P.na + p) * P.nchan + k));
+            const float4 *gq4 = reinterpret_cast<const float4 *>(gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
+            float4 a01 = gp4[0], a23 = gp4[1], b01 = gq4[0], b23 = gq4[1];
+            float2 gp[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
+            float2 gq[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
+            float2 X[4];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    float2 ga = gp[2 * r], gb = gp[2 * r + 1], s0v = Sm[c], s1v = Sm[2 + c];
+                    X[2 * r + c] = make_float2(ga.x * s0v.x - ga.y * s0v.y + gb.x * s1v.x - gb.y * s1v.y,
+                                               ga.x * s0v.y + ga.y * s0v.x + gb.x * s1v.y + gb.y * s1v.x);
+                }
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    float2 x0 = X[2 * r], x1 = X[2 * r + 1], g0 = gq[2 * c], g1 = gq[2 * c + 1];
+                    V[2 * r + c] = make_float2(x0.x * g0.x + x0.y * g0.y + x1.x * g1.x + x1.y * g1.y,
+                                               x0.y * g0.x - x0.x * g0.y + x1.y * g1.x - x1.x * g1.y);
+                }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; c++) V[c] = Sm[c];
+        }
+        const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
+        const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
+        if constexpr (WRITE) {
+            float4 *o = reinterpret_cast<float4 *>(vis + 4 * row);
+            o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
+            o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
+        }
+        if constexpr (CHI2) {
+            const float4 *d4 = reinterpret_cast<const float4 *>(data + 4 * row);
+            float4 d01 = d4[0], d23 = d4[1];
+            float r2 = 0.f, x;
+            x = V[0].x - d01.x; r2 += x * x;
+            x = V[0].y - d01.y; r2 += x * x;
+            x = V[1].x - d01.z; r2 += x * x;
+            x = V[1].y - d01.w; r2 += x * x;
+            x = V[2].x - d23.x; r2 += x * x;
+            x = V[2].y - d23.y; r2 += x * x;
+            x = V[3].x - d23.z; r2 += x * x;
+            x = V[3].y - d23.w; r2 += x * x;
+            chi += (P.has_weight ? weight[row] : 1.f) * r2;
+        }
+    }
+    if constexpr (CHI2) {
+        // thread and warp sums in FP32 (positive terms), block and grid in FP64
+        float w = chi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        double bsum = block_sum<THREADS>((threadIdx.x & 31) == 0 ? (double)w : 0.0, S.red);
+        finish_chi2<THREADS>(bsum, P, S.red, &sLast);
+    }
+}
+}  // namespace f32
+
+// ===========================================================================
+// Host side: work units and launch
+// ===========================================================================
+// Emits the units and tiles of one precision through sink.unit(Unit) and
+// sink.tile(Tile) (each returns false when its storage is full).
+template <typename Sink>
+static bool emit_units(int na, int precision, Sink &sink) {
+    int ntile = 0;
+    auto tile = [&](int p, int q, int fold) {
+        ntile++;
+        return sink.tile(Tile{(uint8_t)p, (uint8_t)q, (uint8_t)fold, 0});
+    };
+    if (precision == RIME_FP64) {
+        using namespace f64;
+        for (int r0 = 0; r0 < na; r0 += ROWS) {
+            int nr = std::min(ROWS, na - r0);
+            Unit d{r0, r0, nr, nr, ntile, 0, 0, 1};
+            for (int pi = 0; pi < nr; pi += TP)
+                for (int qj = 0; qj < nr; qj += TQ)
+                    if (qj + TQ - 1 > pi && !tile(pi, qj, 0)) return false;
+            d.nbody = ntile - d.tile0;
+            if (!sink.unit(d)) return false;
+            for (int c0 = r0 + ROWS; c0 < na; c0 += COLS) {
+                int nc = std::min(COLS, na - c0);
+                Unit o{r0, c0, nr, nc, ntile, 0, 0, 0};
+                for (int pi = 0; pi < nr; pi += TP)
+                    for (int qj = 0; qj < nc; qj += TQ)
+                        if (!tile(pi, qj, 0)) return false;
+                o.nbody = ntile - o.tile0;
+                if (!sink.unit(o)) return false;
+            }
+        }
+        return true;
+    }
+    using namespace f32;
+    for (int r0 = 0; r0 < na; r0 += ROWS) {
+        int nr = std::min(ROWS, na - r0);
+        int nblk = (nr + 7) / 8;
+        // diagonal unit: body tiles (p, 8g) for groups g past p's own 8-block,
+        // then 4 head tiles per 8-block for the pairs inside the block
+        Unit d{r0, r0, nr, nr, ntile, 0, 0, 1};
+        for (int p = 0; p < nr; p++)
+            for (int g = p / 8 + 1; g < nblk; g++)
+                if (!tile(p, 8 * g, 0)) return false;
+        d.nbody = ntile - d.tile0;
+        for (int f = 0; f < 4; f++)
+            for (int m = 0; m < nblk; m++)
+                if (!tile(8 * m, 8 * m, f)) return false;
+        d.nhead = ntile - d.tile0 - d.nbody;
+        if (!sink.unit(d)) return false;
+        for (int c0 = r0 + ROWS; c0 < na; c0 += COLS) {
+            int nc = std::min(COLS, na - c0);
+            Unit o{r0, c0, nr, nc, ntile, 0, 0, 0};
+            for (int p = 0; p < nr; p++)
+                for (int g = 0; 8 * g < nc; g++)
+                    if (!tile(p, 8 * g, 0)) return false;
+            o.nbody = ntile - o.tile0;
+            if (!sink.unit(o)) return false;
+        }
+    }
+    return true;
 }
 
 void build_units(int na, int precision, std::vector<Unit> &units, std::vector<Tile> &tiles) {
-    if (precision == RIME_FP64) build_units_t<double>(na, units, tiles);
-    else build_units_t<float>(na, units, tiles);
-}
-
-// The same work units as build_units, written into caller-provided arrays
-// (no heap use). Returns the number of units, or -1 if an array is too small.
-template <typename T>
-static int build_units_fixed_t(int na, Unit *units, int max_units, Tile *tiles, int max_tiles, int *ntiles) {
-    using S = Shape<T>;
-    int nu = 0, nt = 0;
-    for (int r0 = 0; r0 < na; r0 += S::ROWS) {
-        int nr = std::min(S::ROWS, na - r0);
-        if (nu >= max_units) return -1;
-        Unit d{r0, r0, nr, nr, nt, 0, 1, 0};
-        for (int pi = 0; pi < nr; pi += S::TP)
-            for (int qj = 0; qj < nr; qj += S::TQ)
-                if (qj + S::TQ - 1 > pi) {
-                    if (nt >= max_tiles) return -1;
-                    tiles[nt++] = Tile{(uint8_t)pi, (uint8_t)qj};
-                }
-        d.ntiles = nt - d.tile0;
-        units[nu++] = d;
-        for (int c0 = r0 + S::ROWS; c0 < na; c0 += S::COLS) {
-            int nc = std::min(S::COLS, na - c0);
-            if (nu >= max_units) return -1;
-            Unit u{r0, c0, nr, nc, nt, 0, 0, 0};
-            for (int pi = 0; pi < nr; pi += S::TP)
-                for (int qj = 0; qj < nc; qj += S::TQ) {
-                    if (nt >= max_tiles) return -1;
-                    tiles[nt++] = Tile{(uint8_t)pi, (uint8_t)qj};
-                }
-            u.ntiles = nt - u.tile0;
-            units[nu++] = u;
-        }
-    }
-    *ntiles = nt;
-    return nu;
+    struct {
+        std::vector<Unit> *u;
+        std::vector<Tile> *t;
+        bool unit(const Unit &x) { u->push_back(x); return true; }
+        bool tile(const Tile &x) { t->push_back(x); return true; }
+    } sink{&units, &tiles};
+    units.clear();
+    tiles.clear();
+    emit_units(na, precision, sink);
 }
 
 int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
                       int *ntiles) {
-    return precision == RIME_FP64 ? build_units_fixed_t<double>(na, units, max_units, tiles, max_tiles, ntiles)
-                                  : build_units_fixed_t<float>(na, units, max_units, tiles, max_tiles, ntiles);
+    struct {
+        Unit *u;
+        Tile *t;
+        int mu, mt, nu = 0, nt = 0;
+        bool unit(const Unit &x) { if (nu >= mu) return false; u[nu++] = x; return true; }
+        bool tile(const Tile &x) { if (nt >= mt) return false; t[nt++] = x; return true; }
+    } sink{units, tiles, max_units, max_tiles};
+    if (!emit_units(na, precision, sink)) return -1;
+    *ntiles = sink.nt;
+    return sink.nu;
 }
 
 int fused_blocks(const rime_ctx *c) { return c->dims.ntime * c->dims.nchan * c->nunits; }
 
-template <typename T, bool CHI2, bool WRITE>
-static cudaError_t launch_t(const FusedParams &P, int blocks, cudaStream_t stream) {
-    size_t smem = Smem<T>::bytes();
+template <typename K>
+static cudaError_t launch_k(K kernel, const FusedParams &P, int blocks, int threads, size_t smem,
+                            cudaStream_t stream) {
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<T, CHI2, WRITE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_fused<T, CHI2, WRITE><<<blocks, Shape<T>::THREADS, smem, stream>>>(P);
+    kernel<<<blocks, threads, smem, stream>>>(P);
     return cudaGetLastError();
 }
 
@@ -501,6 +834,7 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
     P.nunits = c->nunits;
     P.has_gains = c->has_gains;
     P.has_weight = c->has_weight;
+    P.has_pointing = c->has_pointing;
     P.units = c->d_units;
     P.tiles = c->d_tiles;
     P.chan = c->d_chan;
@@ -521,12 +855,14 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
     P.status = c->d_status;
     int blocks = fused_blocks(c);
     if (blocks == 0) return cudaSuccess;
-    bool f64 = c->dims.precision == RIME_FP64;
-    if (chi2)
-        return f64 ? launch_t<double, true, false>(P, blocks, c->stream)
-                   : launch_t<float, true, false>(P, blocks, c->stream);
-    return f64 ? launch_t<double, false, true>(P, blocks, c->stream)
-               : launch_t<float, false, true>(P, blocks, c->stream);
+    if (c->dims.precision == RIME_FP64) {
+        size_t sm = f64::smem_bytes();
+        return chi2 ? launch_k(f64::k_fused_f64<true, false>, P, blocks, f64::THREADS, sm, c->stream)
+                    : launch_k(f64::k_fused_f64<false, true>, P, blocks, f64::THREADS, sm, c->stream);
+    }
+    size_t sm = sizeof(f32::Smem);
+    return chi2 ? launch_k(f32::k_fused_f32<true, false>, P, blocks, f32::THREADS, sm, c->stream)
+                : launch_k(f32::k_fused_f32<false, true>, P, blocks, f32::THREADS, sm, c->stream);
 }
 
 }  // namespace rime

@@ -47,17 +47,23 @@ struct DevStatus {
 };
 
 // A unit of work for one thread block: antenna rows [r0, r0+nr) against
-// columns [c0, c0+nc), with the list of thread tiles in tiles[tile0 ..
-// tile0+ntiles). diag = 1 when rows and columns are the same antennas.
+// columns [c0, c0+nc) (diag = 1: the same antennas, pairs p < q only). Its
+// thread tiles are tiles[tile0 .. tile0+nbody) ("body" tiles, thread tid <
+// nbody) followed by nhead "head" tiles that start at the first warp boundary
+// after the body tiles (FP32 kernel only).
 struct Unit {
     int32_t r0, c0, nr, nc;
-    int32_t tile0, ntiles;
-    int32_t diag, pad;
+    int32_t tile0, nbody, nhead, diag;
 };
-// A thread tile: its first row antenna and first column antenna, relative
-// to the unit's r0 / c0.
+// A thread tile, antennas relative to the unit's r0 / c0.
+//  FP32 body tile: row antenna p, column antennas q .. q+7.
+//  FP32 head tile: pairs inside the 8-antenna block starting at p (= q):
+//                  with x_i = p + ((fold + i) mod 8), the seven pairs
+//                  (x_0, x_1..x_4) and (x_4, x_5..x_7); folds 0..3 cover the
+//                  block's 28 pairs once (round-robin by cyclic distance).
+//  FP64 tile:      row antennas p, p+1 against columns q, q+1.
 struct Tile {
-    uint8_t p, q;
+    uint8_t p, q, fold, pad;
 };
 
 // Per-channel constants, single precision path.
@@ -82,7 +88,7 @@ struct FusedParams {
     int stokes_tstride;        // nsrc*4 if time varying, else 0 (elements)
     int nchp;                  // channel groups per timestep
     int nunits;
-    int has_gains, has_weight;
+    int has_gains, has_weight, has_pointing;
     const Unit *units;
     const Tile *tiles;
     const void *chan;          // ChanF* or ChanD*
