@@ -148,6 +148,22 @@ rime_status rime_chi2(rime_ctx *ctx, double *chi2);
  * double) and does not wait; suitable for CUDA graph capture. */
 rime_status rime_chi2_async(rime_ctx *ctx, double *chi2_dev);
 
+/* chi^2 (eq. 7) and its gradient: the adjoint of eqs. 1-7 with respect to
+ * every source parameter and every gain, recomputing K and E (eqs. 3-4)
+ * rather than storing them. Waits for the stream.
+ *   chi2        host pointer, receives chi^2 (the same value rime_chi2 gives)
+ *   grad_src    device [nsrc][10] double: d chi^2 / d(l, m, I, Q, U, V, alpha,
+ *               major, minor, pa) (the shape derivatives are 0 for points)
+ *   grad_gains  device [ntime][na][nchan][4] complex128, or NULL: the complex
+ *               gradient d chi^2/dRe G + i d chi^2/dIm G of each Jones entry
+ *               (with identity gains when none are set)
+ * Needs static brightness (time_varying = 0), else RIME_E_INVALID. Uses a
+ * device buffer of one complex Y_X per visibility and correlation and one
+ * partial per (t, channel, antenna unit, source), allocated on first use.
+ * The gains gradient is summed with floating-point atomics (not bit-for-bit
+ * reproducible across runs); the source gradient is summed in a fixed order. */
+rime_status rime_chi2_grad(rime_ctx *ctx, double *chi2, double *grad_src, void *grad_gains);
+
 /* sum over visibilities of ln(2 pi / w) (the second term of eq. 7), so that
  * -2 ln L = chi^2 + rime_ln_norm. Waits for the stream. */
 rime_status rime_ln_norm(rime_ctx *ctx, double *ln_norm);

@@ -57,6 +57,7 @@ def lib():
         L.rime_predict.argtypes = [vp, vp]
         L.rime_chi2.argtypes = [vp, C.POINTER(C.c_double)]
         L.rime_chi2_async.argtypes = [vp, vp]
+        L.rime_chi2_grad.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
         L.rime_ln_norm.argtypes = [vp, C.POINTER(C.c_double)]
         L.rime_sync.argtypes = [vp]
         L.rime_destroy.argtypes, L.rime_destroy.restype = [vp], None
@@ -64,7 +65,7 @@ def lib():
                                         C.POINTER(rime_sources), vp, vp]
         L.rime_chi2_noalloc.restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
-                  "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async",
+                  "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
                   "rime_ln_norm", "rime_sync"):
             getattr(L, f).restype = ip
         _lib = L
@@ -193,6 +194,16 @@ def rime_chi2(ctx) -> float:
 def rime_chi2_async(ctx, chi2_dev):
     """chi2_dev: a float64 device tensor with at least one element."""
     _check(lib().rime_chi2_async(ctx, chi2_dev.data_ptr()), ctx)
+
+
+def rime_chi2_grad(ctx, grad_src, grad_gains=None) -> float:
+    """grad_src: float64 device tensor [nsrc][10]; grad_gains: complex128 device
+    tensor [ntime][na][nchan][2][2] or None. Returns chi^2."""
+    out = C.c_double()
+    gs = grad_src.data_ptr() if grad_src is not None and grad_src.numel() else None
+    gg = grad_gains.data_ptr() if grad_gains is not None else None
+    _check(lib().rime_chi2_grad(ctx, C.byref(out), gs, gg), ctx)
+    return out.value
 
 
 def rime_ln_norm(ctx) -> float:

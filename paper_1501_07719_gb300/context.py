@@ -24,6 +24,7 @@ class Rime:
         self.cdtype = torch.complex128 if precision == A.RIME_FP64 else torch.complex64
         self.rdtype = torch.float64 if precision == A.RIME_FP64 else torch.float32
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.nsrc = 0
         self.ctx = A.rime_create(self.na, self.ntime, self.nchan, precision, obs["freq"], obs["uvw"],
                                  obs.get("pointing"), data, weight, self.stream.cuda_stream,
                                  float(obs["ref_freq_hz"]), float(obs["beam_c"]))
@@ -40,6 +41,7 @@ class Rime:
 
     def set_sources(self, src: dict):
         A.rime_set_sources(self.ctx, src["lm"], src["stokes"], src["alpha"], src.get("shape"))
+        self.nsrc = int(src["alpha"].shape[0])
 
     # calls ------------------------------------------------------------------
     def predict(self, out=None):
@@ -55,6 +57,19 @@ class Rime:
     def chi2_async(self, out):
         A.rime_chi2_async(self.ctx, out)
         return out
+
+    def chi2_grad(self, want_gains: bool = True):
+        """chi^2, d chi^2 / d(source parameters) as a [nsrc, 10] float64 device
+        tensor (l, m, I, Q, U, V, alpha, major, minor, pa) and, if requested,
+        d chi^2 / dG as a [ntime, na, nchan, 2, 2] complex128 device tensor."""
+        nsrc = self.nsrc
+        gs = self.torch.zeros((nsrc, 10), dtype=self.torch.float64, device="cuda")
+        gg = None
+        if want_gains:
+            gg = self.torch.zeros((self.ntime, self.na, self.nchan, 2, 2), dtype=self.torch.complex128,
+                                  device="cuda")
+        chi = A.rime_chi2_grad(self.ctx, gs, gg)
+        return chi, gs, gg
 
     def ln_norm(self) -> float:
         return A.rime_ln_norm(self.ctx)

@@ -66,8 +66,9 @@ struct Alloc {
 void free_all(rime_ctx *c) {
     void *ptrs[] = {c->d_freq, c->d_chan, c->d_uvw, c->d_uvw_f, c->d_pointing, c->d_data,
                     c->d_weight, c->d_gains_in, c->d_gains, c->d_src_in, c->d_stokes,
-                    c->d_gauss, c->d_alpha, c->d_tau, c->d_rho, c->d_units, c->d_tiles,
-                    c->d_partials, c->d_counter, c->d_status};
+                    c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho, c->d_units,
+                    c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
+                    c->d_gunits, c->d_gbl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_status) cudaFreeHost(c->h_status);
@@ -312,11 +313,14 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
     size_t nd = (size_t)c->dims.ntime * n * c->dims.na;
     if (nd > (size_t)LLONG_MAX / 16) return fail(c, RIME_E_INVALID, "nsrc too large");
     if (n > c->src_cap || rows != c->src_stokes_rows) {
-        void *old[] = {c->d_src_in, c->d_stokes, c->d_gauss, c->d_alpha, c->d_tau, c->d_rho};
+        void *old[] = {c->d_src_in, c->d_stokes, c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho,
+                       c->d_gpart};
         for (void *p : old)
             if (p) cudaFree(p);
         c->d_src_in = nullptr;
-        c->d_stokes = c->d_gauss = c->d_alpha = c->d_tau = c->d_rho = nullptr;
+        c->d_stokes = c->d_gauss = c->d_alpha = c->d_src_extra = c->d_tau = c->d_rho = nullptr;
+        c->d_gpart = nullptr;
+        c->gpart_cap = 0;
         c->src_cap = 0;
         c->sources_set = false;
         size_t cap = std::max<size_t>(n, 1);
@@ -327,6 +331,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
         CK(c, alloc(&c->d_stokes, rows * cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_gauss, cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_alpha, cap * ts), "allocating sources");
+        CK(c, alloc(&c->d_src_extra, cap * 8 * ts), "allocating sources");
         CK(c, alloc(&c->d_tau, ndc * 8), "allocating delays");
         CK(c, alloc(&c->d_rho, ndc * ts), "allocating delays");
         c->src_cap = cap;
@@ -375,6 +380,28 @@ rime_status rime_chi2(rime_ctx *c, double *chi2) {
     rime_status s = rime_chi2_async(c, &c->d_status->chi2);
     if (s != RIME_OK) return s;
     s = sync_status(c);
+    if (s != RIME_OK) return s;
+    *chi2 = c->h_status->chi2;
+    return RIME_OK;
+}
+
+rime_status rime_chi2_grad(rime_ctx *c, double *chi2, double *grad_src, void *grad_gains) {
+    if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
+    if (!chi2) return fail(c, RIME_E_INVALID, "chi2 is NULL");
+    if (!c->sources_set) return fail(c, RIME_E_STATE, "rime_set_sources has not been called");
+    if (!c->has_data) return fail(c, RIME_E_STATE, "no observed data (rime_set_data)");
+    if (c->time_varying)
+        return fail(c, RIME_E_INVALID, "the gradient needs static brightness (time_varying = 0)");
+    if (c->nsrc > 0 && !grad_src) return fail(c, RIME_E_INVALID, "grad_src is NULL");
+    Alloc alloc{c};
+    if (!c->d_yadj) CK(c, alloc(&c->d_yadj, vis_count(c) * 4 * 2 * c->tsize()), "allocating the adjoint buffer");
+    double *gg = static_cast<double *>(grad_gains);
+    if (gg)
+        CK(c, cudaMemsetAsync(gg, 0, (size_t)c->dims.ntime * c->dims.na * c->dims.nchan * 8 * sizeof(double),
+                              c->stream), "clearing grad_gains");
+    CK(c, launch_fused_mode(c, MODE_GRAD, nullptr, &c->d_status->chi2, c->d_yadj, gg), "gradient forward kernel");
+    CK(c, launch_grad_src(c, grad_src), "source gradient kernels");
+    rime_status s = sync_status(c);
     if (s != RIME_OK) return s;
     *chi2 = c->h_status->chi2;
     return RIME_OK;

@@ -108,6 +108,66 @@ __device__ void finish_chi2(double block_value, const FusedParams &P, double *re
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2x2 complex matrices (row-major 00, 01, 10, 11) for the epilogues
+// ---------------------------------------------------------------------------
+template <typename T2> __device__ __forceinline__ T2 cmk(double x, double y);
+template <> __device__ __forceinline__ float2 cmk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+template <> __device__ __forceinline__ double2 cmk<double2>(double x, double y) { return make_double2(x, y); }
+template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {   // a conj(b)
+    T2 r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
+}
+template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T2> __device__ __forceinline__ T2 cconj(T2 a) { T2 r; r.x = a.x; r.y = -a.y; return r; }
+template <typename T2> __device__ __forceinline__ void mmul(const T2 *a, const T2 *b, T2 *o) {
+    T2 r0 = cadd(cmul(a[0], b[0]), cmul(a[1], b[2])), r1 = cadd(cmul(a[0], b[1]), cmul(a[1], b[3]));
+    T2 r2 = cadd(cmul(a[2], b[0]), cmul(a[3], b[2])), r3 = cadd(cmul(a[2], b[1]), cmul(a[3], b[3]));
+    o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3;
+}
+template <typename T2> __device__ __forceinline__ void mherm(const T2 *a, T2 *o) {
+    T2 r1 = cconj(a[2]), r2 = cconj(a[1]);
+    o[0] = cconj(a[0]); o[1] = r1; o[2] = r2; o[3] = cconj(a[3]);
+}
+
+// Adjoint of the chi^2 term of one visibility (eq. 7 through eq. 1):
+//   Sh = 2 w G_p^H R G_q with R = V - D; for a source with coherency c B0
+//   (eq. 2), d chi^2 = Re(c sum_X X Y_X) with
+//   Y_I = conj(Sh00 + Sh11), Y_Q = conj(Sh00 - Sh11), Y_U = conj(Sh01 + Sh10),
+//   Y_V = i conj(Sh01 - Sh10);
+//   dchi^2/dG_p = 2 w R G_q S^H, dchi^2/dG_q = 2 w R^H G_p S  (complex
+//   gradient d/dRe + i d/dIm).
+template <typename T, typename T2>
+__device__ __forceinline__ void grad_terms(const T2 *V, const T2 *Sm, const T2 *D, T w, const T2 *gp, const T2 *gq,
+                                           T2 *Y, T2 *dGp, T2 *dGq) {
+    T2 R[4], Sh[4], tmp[4], gh[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        R[c] = csub(V[c], D[c]);
+        R[c].x *= 2 * w;
+        R[c].y *= 2 * w;
+    }
+    mherm(gp, gh);
+    mmul(gh, R, tmp);
+    mmul(tmp, gq, Sh);
+    Y[0] = cconj(cadd(Sh[0], Sh[3]));
+    Y[1] = cconj(csub(Sh[0], Sh[3]));
+    Y[2] = cconj(cadd(Sh[1], Sh[2]));
+    T2 d = csub(Sh[1], Sh[2]);
+    Y[3].x = d.y;
+    Y[3].y = d.x;
+    T2 sh[4];
+    mherm(Sm, sh);
+    mmul(R, gq, tmp);
+    mmul(tmp, sh, dGp);
+    mherm(R, gh);
+    mmul(gh, gp, tmp);
+    mmul(tmp, Sm, dGq);
+}
+
 // ===========================================================================
 // FP64 kernel: 2 x 2 antenna tiles, 32-antenna units
 // ===========================================================================
@@ -118,7 +178,11 @@ constexpr int THREADS = 256;
 constexpr int SC = 16;
 constexpr int ASTRIDE = ROWS + 4;
 struct D4 { double x, y, z, w; };
-constexpr size_t smem_bytes() { return 2 * SC * ASTRIDE * sizeof(double2) + 2 * SC * sizeof(D4) + 64 * sizeof(double); }
+constexpr int NLOCMAX = ROWS + COLS;
+constexpr size_t smem_bytes() {
+    return 2 * SC * ASTRIDE * sizeof(double2) + 2 * SC * sizeof(D4) + 64 * sizeof(double) +
+           NLOCMAX * 8 * sizeof(double);
+}
 
 __device__ __forceinline__ double2 antenna_factor(double tau, double rho, double alpha, const ChanD &ch) {
     double ph = ch.nu * tau;                 // eq. 3 phase in turns
@@ -132,13 +196,15 @@ __device__ __forceinline__ double2 antenna_factor(double tau, double rho, double
     return make_double2(amp * cs, amp * sn);
 }
 
-template <bool CHI2, bool WRITE>
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
+    constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *sA = reinterpret_cast<double2 *>(smem_raw);            // [2][SC][ASTRIDE]
     D4 *sSt = reinterpret_cast<D4 *>(sA + 2 * SC * ASTRIDE);         // [SC]
     D4 *sGq = sSt + SC;                                              // [SC]
     double *sRed = reinterpret_cast<double *>(sGq + SC);             // [64]
+    double *sGG = sRed + 64;                                         // [NLOCMAX][8] gains gradient
     __shared__ int sLast;
 
     if (inputs_bad(P.status)) return;
@@ -249,6 +315,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     const double2 *data = reinterpret_cast<const double2 *>(P.data);
     const double *weight = reinterpret_cast<const double *>(P.weight);
     double2 *vis = reinterpret_cast<double2 *>(P.vis_out);
+    if constexpr (GRAD) {
+        for (int i = tid; i < NLOCMAX * 8; i += THREADS) sGG[i] = 0.0;
+        __syncthreads();
+    }
+    const double2 I2[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
 #pragma unroll
     for (int i = 0; i < TP; i++)
 #pragma unroll
@@ -261,31 +332,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
             Sm[1] = make_double2(acc[b][4] - acc[b][7], acc[b][5] + acc[b][6]);   // U + iV
             Sm[2] = make_double2(acc[b][4] + acc[b][7], acc[b][5] - acc[b][6]);   // U - iV
             Sm[3] = make_double2(acc[b][0] - acc[b][2], acc[b][1] - acc[b][3]);   // I - Q
-            double2 V[4];
-            if (P.has_gains) {
-                const double2 *gp = gains + 4 * (((long long)t * P.na + p) * P.nchan + k);
-                const double2 *gq = gains + 4 * (((long long)t * P.na + q) * P.nchan + k);
-                double2 X[4];
+            double2 gp[4], gq[4], V[4], tmp[4], gqh[4];
 #pragma unroll
-                for (int r = 0; r < 2; r++)
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        double2 a = gp[2 * r], bb = gp[2 * r + 1], s0v = Sm[c], s1v = Sm[2 + c];
-                        X[2 * r + c] = make_double2(a.x * s0v.x - a.y * s0v.y + bb.x * s1v.x - bb.y * s1v.y,
-                                                    a.x * s0v.y + a.y * s0v.x + bb.x * s1v.y + bb.y * s1v.x);
-                    }
-#pragma unroll
-                for (int r = 0; r < 2; r++)
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        double2 x0 = X[2 * r], x1 = X[2 * r + 1], g0 = gq[2 * c], g1 = gq[2 * c + 1];
-                        V[2 * r + c] = make_double2(x0.x * g0.x + x0.y * g0.y + x1.x * g1.x + x1.y * g1.y,
-                                                    x0.y * g0.x - x0.x * g0.y + x1.y * g1.x - x1.x * g1.y);
-                    }
-            } else {
-#pragma unroll
-                for (int c = 0; c < 4; c++) V[c] = Sm[c];
+            for (int c = 0; c < 4; c++) {
+                gp[c] = P.has_gains ? gains[4 * (((long long)t * P.na + p) * P.nchan + k) + c] : I2[c];
+                gq[c] = P.has_gains ? gains[4 * (((long long)t * P.na + q) * P.nchan + k) + c] : I2[c];
             }
+            mmul(gp, Sm, tmp);      // eq. 1: V = G_p S G_q^H
+            mherm(gq, gqh);
+            mmul(tmp, gqh, V);
             const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
             const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
             if constexpr (WRITE) {
@@ -293,16 +348,42 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
                 for (int c = 0; c < 4; c++) vis[4 * row + c] = V[c];
             }
             if constexpr (CHI2) {
+                double2 D[4];
                 double r2 = 0.0;
 #pragma unroll
                 for (int c = 0; c < 4; c++) {
-                    double2 d = data[4 * row + c];
-                    double dr = V[c].x - d.x, di = V[c].y - d.y;
+                    D[c] = data[4 * row + c];
+                    double dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
                     r2 += dr * dr + di * di;
                 }
-                chi += (P.has_weight ? weight[row] : 1.0) * r2;
+                const double w = P.has_weight ? weight[row] : 1.0;
+                chi += w * r2;
+                if constexpr (GRAD) {
+                    double2 Y[4], dGp[4], dGq[4];
+                    grad_terms<double, double2>(V, Sm, D, w, gp, gq, Y, dGp, dGq);
+                    double2 *yo = reinterpret_cast<double2 *>(P.yout) + 4 * row;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) yo[c] = Y[c];
+                    const int lp = p - U.r0, lq = U.diag ? q - U.r0 : U.nr + (q - U.c0);
+                    if (P.grad_gains)
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        atomicAdd(&sGG[lp * 8 + 2 * c], dGp[c].x);
+                        atomicAdd(&sGG[lp * 8 + 2 * c + 1], dGp[c].y);
+                        atomicAdd(&sGG[lq * 8 + 2 * c], dGq[c].x);
+                        atomicAdd(&sGG[lq * 8 + 2 * c + 1], dGq[c].y);
+                    }
+                }
             }
         }
+    if constexpr (GRAD) {
+        __syncthreads();
+        for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
+            const int a = i >> 3;
+            const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+            atomicAdd(&P.grad_gains[8 * (((long long)t * P.na + ant) * P.nchan + k) + (i & 7)], sGG[i]);
+        }
+    }
     if constexpr (CHI2) {
         double bsum = block_sum<THREADS>(chi, sRed);
         finish_chi2<THREADS>(bsum, P, sRed, &sLast);
@@ -351,6 +432,7 @@ struct Smem {
     float4 St[SC][2];           // (I, I, Q, Q), (U, U, V, V), scaled (see staging)
     float Gf[SC];               // 1 for a Gaussian source
     float2 uv[NLOC];            // antenna (u, v) at this timestep, unit order
+    float GG[NLOC * 8];         // gradient mode: per-antenna gains gradient of this block
     double red[32];
 };
 
@@ -431,8 +513,9 @@ __device__ __forceinline__ float2 gauss2(float2 qp, float2 up, float2 vp, float2
     return f2(ex2_approx(e.x), ex2_approx(e.y));
 }
 
-template <bool CHI2, bool WRITE>
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
+    constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     __shared__ int sLast;
@@ -639,6 +722,11 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const float2 *data = reinterpret_cast<const float2 *>(P.data);
     const float *weight = reinterpret_cast<const float *>(P.weight);
     float2 *vis = reinterpret_cast<float2 *>(P.vis_out);
+    if constexpr (GRAD) {
+        for (int i = tid; i < NLOC * 8; i += THREADS) S.GG[i] = 0.f;
+        __syncthreads();
+    }
+    const float2 I2[4] = {f2(1.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(1.f, 0.f)};
 #pragma unroll
     for (int j = 0; j < NSLOT; j++) {
         if (!((mask >> j) & 1u)) continue;
@@ -659,34 +747,21 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
         Sm[1] = make_float2(Ur - Vi, Ui + Vr);   // U + iV
         Sm[2] = make_float2(Ur + Vi, Ui - Vr);   // U - iV
         Sm[3] = make_float2(Ir - Qr, Ii - Qi);   // I - Q
-        float2 V[4];
+        float2 gp[4], gq[4];
         if (P.has_gains) {
             const float4 *gp4 = reinterpret_cast<const float4 *>(gains + 4 * (((long long)t * P.na + p) * P.nchan + k));
             const float4 *gq4 = reinterpret_cast<const float4 *>(gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
-            float4 a01 = gp4[0], a23 = gp4[1], b01 = gq4[0], b23 = gq4[1];
-            float2 gp[4] = {{a01.x, a01.y}, {a01.z, a01.w}, {a23.x, a23.y}, {a23.z, a23.w}};
-            float2 gq[4] = {{b01.x, b01.y}, {b01.z, b01.w}, {b23.x, b23.y}, {b23.z, b23.w}};
-            float2 X[4];
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    float2 ga = gp[2 * r], gb = gp[2 * r + 1], s0v = Sm[c], s1v = Sm[2 + c];
-                    X[2 * r + c] = make_float2(ga.x * s0v.x - ga.y * s0v.y + gb.x * s1v.x - gb.y * s1v.y,
-                                               ga.x * s0v.y + ga.y * s0v.x + gb.x * s1v.y + gb.y * s1v.x);
-                }
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    float2 x0 = X[2 * r], x1 = X[2 * r + 1], g0 = gq[2 * c], g1 = gq[2 * c + 1];
-                    V[2 * r + c] = make_float2(x0.x * g0.x + x0.y * g0.y + x1.x * g1.x + x1.y * g1.y,
-                                               x0.y * g0.x - x0.x * g0.y + x1.y * g1.x - x1.x * g1.y);
-                }
+            const float4 a01 = gp4[0], a23 = gp4[1], b01 = gq4[0], b23 = gq4[1];
+            gp[0] = f2(a01.x, a01.y); gp[1] = f2(a01.z, a01.w); gp[2] = f2(a23.x, a23.y); gp[3] = f2(a23.z, a23.w);
+            gq[0] = f2(b01.x, b01.y); gq[1] = f2(b01.z, b01.w); gq[2] = f2(b23.x, b23.y); gq[3] = f2(b23.z, b23.w);
         } else {
 #pragma unroll
-            for (int c = 0; c < 4; c++) V[c] = Sm[c];
+            for (int c = 0; c < 4; c++) gp[c] = gq[c] = I2[c];
         }
+        float2 V[4], tmp[4], gqh[4];
+        mmul(gp, Sm, tmp);      // eq. 1: V = G_p S G_q^H
+        mherm(gq, gqh);
+        mmul(tmp, gqh, V);
         const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
         const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
         if constexpr (WRITE) {
@@ -696,17 +771,40 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
         }
         if constexpr (CHI2) {
             const float4 *d4 = reinterpret_cast<const float4 *>(data + 4 * row);
-            float4 d01 = d4[0], d23 = d4[1];
-            float r2 = 0.f, x;
-            x = V[0].x - d01.x; r2 += x * x;
-            x = V[0].y - d01.y; r2 += x * x;
-            x = V[1].x - d01.z; r2 += x * x;
-            x = V[1].y - d01.w; r2 += x * x;
-            x = V[2].x - d23.x; r2 += x * x;
-            x = V[2].y - d23.y; r2 += x * x;
-            x = V[3].x - d23.z; r2 += x * x;
-            x = V[3].y - d23.w; r2 += x * x;
-            chi += (P.has_weight ? weight[row] : 1.f) * r2;
+            const float4 d01 = d4[0], d23 = d4[1];
+            const float2 D[4] = {f2(d01.x, d01.y), f2(d01.z, d01.w), f2(d23.x, d23.y), f2(d23.z, d23.w)};
+            float r2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
+                r2 += dr * dr + di * di;
+            }
+            const float w = P.has_weight ? weight[row] : 1.f;
+            chi += w * r2;
+            if constexpr (GRAD) {
+                float2 Y[4], dGp[4], dGq[4];
+                grad_terms<float, float2>(V, Sm, D, w, gp, gq, Y, dGp, dGq);
+                float4 *yo = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(P.yout) + 4 * row);
+                yo[0] = make_float4(Y[0].x, Y[0].y, Y[1].x, Y[1].y);
+                yo[1] = make_float4(Y[2].x, Y[2].y, Y[3].x, Y[3].y);
+                const int lp = pj, lq = U.diag ? qj : U.nr + qj;
+                if (P.grad_gains)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    atomicAdd(&S.GG[lp * 8 + 2 * c], dGp[c].x);
+                    atomicAdd(&S.GG[lp * 8 + 2 * c + 1], dGp[c].y);
+                    atomicAdd(&S.GG[lq * 8 + 2 * c], dGq[c].x);
+                    atomicAdd(&S.GG[lq * 8 + 2 * c + 1], dGq[c].y);
+                }
+            }
+        }
+    }
+    if constexpr (GRAD) {
+        __syncthreads();
+        for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
+            const int la = i >> 3;
+            const int ant = la < U.nr ? U.r0 + la : U.c0 + (la - U.nr);
+            atomicAdd(&P.grad_gains[8 * (((long long)t * P.na + ant) * P.nchan + k) + (i & 7)], (double)S.GG[i]);
         }
     }
     if constexpr (CHI2) {
@@ -823,6 +921,11 @@ static cudaError_t launch_k(K kernel, const FusedParams &P, int blocks, int thre
 }
 
 cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) {
+    return launch_fused_mode(c, chi2 ? MODE_CHI2 : MODE_PREDICT, vis_out, result, nullptr, nullptr);
+}
+
+cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
+                              double *grad_gains) {
     FusedParams P{};
     P.na = c->dims.na;
     P.ntime = c->dims.ntime;
@@ -853,16 +956,24 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
     P.counter = c->d_counter;
     P.result = result;
     P.status = c->d_status;
+    P.yout = yout;
+    P.grad_gains = grad_gains;
     int blocks = fused_blocks(c);
     if (blocks == 0) return cudaSuccess;
     if (c->dims.precision == RIME_FP64) {
         size_t sm = f64::smem_bytes();
-        return chi2 ? launch_k(f64::k_fused_f64<true, false>, P, blocks, f64::THREADS, sm, c->stream)
-                    : launch_k(f64::k_fused_f64<false, true>, P, blocks, f64::THREADS, sm, c->stream);
+        switch (mode) {
+            case MODE_PREDICT: return launch_k(f64::k_fused_f64<MODE_PREDICT>, P, blocks, f64::THREADS, sm, c->stream);
+            case MODE_CHI2: return launch_k(f64::k_fused_f64<MODE_CHI2>, P, blocks, f64::THREADS, sm, c->stream);
+            default: return launch_k(f64::k_fused_f64<MODE_GRAD>, P, blocks, f64::THREADS, sm, c->stream);
+        }
     }
     size_t sm = sizeof(f32::Smem);
-    return chi2 ? launch_k(f32::k_fused_f32<true, false>, P, blocks, f32::THREADS, sm, c->stream)
-                : launch_k(f32::k_fused_f32<false, true>, P, blocks, f32::THREADS, sm, c->stream);
+    switch (mode) {
+        case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT>, P, blocks, f32::THREADS, sm, c->stream);
+        case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2>, P, blocks, f32::THREADS, sm, c->stream);
+        default: return launch_k(f32::k_fused_f32<MODE_GRAD>, P, blocks, f32::THREADS, sm, c->stream);
+    }
 }
 
 }  // namespace rime

@@ -107,7 +107,13 @@ struct FusedParams {
     unsigned int *counter;     // completion counter (reset by the last block)
     double *result;            // where the last block stores chi^2
     const DevStatus *status;   // kernels skip their work if any err word is set
+    // gradient mode only
+    void *yout;                // complex T [ntime][nbl][nchan][4]: Stokes-projected adjoint Y_X
+    double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
 };
+
+// Kernel modes of the fused predict / chi^2 kernels.
+enum FusedMode { MODE_PREDICT = 0, MODE_CHI2 = 1, MODE_GRAD = 2 };
 
 // Checks on the status block that every kernel makes before working.
 __device__ __forceinline__ bool inputs_bad(const DevStatus *st) {
@@ -152,6 +158,14 @@ struct rime_ctx {
     double *src_shape() const { return src_alpha() + src_cap; }
     bool has_shape = false;
     void *d_stokes = nullptr, *d_gauss = nullptr, *d_alpha = nullptr;
+    void *d_src_extra = nullptr;      // per source: l, m, l/n, m/n, major, minor, sin pa, cos pa
+    // gradient scratch (allocated by the first rime_chi2_grad)
+    void *d_yadj = nullptr;           // Y_X per visibility
+    double *d_gpart = nullptr;        // per (t, k, unit) partial source gradients
+    size_t gpart_cap = 0;
+    rime::Unit *d_gunits = nullptr;   // gradient work units and their baseline lists
+    uint16_t *d_gbl = nullptr;
+    int ngunits = 0;
     void *d_tau = nullptr, *d_rho = nullptr;
     // work decomposition
     rime::Unit *d_units = nullptr;
@@ -176,8 +190,12 @@ cudaError_t launch_convert_gains(rime_ctx *c);
 cudaError_t launch_prep_sources(rime_ctx *c);
 cudaError_t launch_prep_delays(rime_ctx *c);
 cudaError_t launch_ln_norm(rime_ctx *c);
+// rime_grad.cu
+cudaError_t launch_grad_src(rime_ctx *c, double *grad_src);
 // launchers (rime_fused.cu)
 cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2);
+cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
+                              double *grad_gains);
 int fused_blocks(const rime_ctx *c);
 int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
                       int *ntiles);

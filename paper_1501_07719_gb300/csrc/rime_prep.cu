@@ -94,7 +94,7 @@ __global__ void k_convert_gains(long long n, const double *in, T *out, DevStatus
 template <typename T>
 __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, const double *stokes,
                                const double *alpha, const double *shape, T *o_stokes, T *o_gauss,
-                               T *o_alpha, DevStatus *st) {
+                               T *o_alpha, T *o_extra, DevStatus *st) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nst = (long long)stokes_rows * nsrc;
     if (i < nst) {
@@ -132,6 +132,13 @@ __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, cons
     o_gauss[4 * i + 2] = (T)C;
     o_gauss[4 * i + 3] = gauss ? T(1) : T(0);
     o_alpha[i] = (T)a;
+    if (o_extra) {
+        // for the gradient: l, m, l/n, m/n, major, minor, sin pa, cos pa
+        double n = sqrt(1.0 - (l * l + m * m));
+        T *x = o_extra + 8 * i;
+        x[0] = (T)l; x[1] = (T)m; x[2] = (T)(l / n); x[3] = (T)(m / n);
+        x[4] = (T)maj; x[5] = (T)mn; x[6] = (T)sp; x[7] = (T)cp;
+    }
 }
 
 // Per (t, s, a): geometric delay tau = (u l + v m + w (n - 1)) / c in
@@ -242,11 +249,11 @@ cudaError_t launch_prep_sources(rime_ctx *c) {
     if (c->dims.precision == RIME_FP64)
         k_prep_sources<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
             nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (double *)c->d_stokes,
-            (double *)c->d_gauss, (double *)c->d_alpha, c->d_status);
+            (double *)c->d_gauss, (double *)c->d_alpha, (double *)c->d_src_extra, c->d_status);
     else
         k_prep_sources<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
             nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (float *)c->d_stokes,
-            (float *)c->d_gauss, (float *)c->d_alpha, c->d_status);
+            (float *)c->d_gauss, (float *)c->d_alpha, (float *)c->d_src_extra, c->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_prep_delays(c);
