@@ -727,6 +727,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
         __syncthreads();
     }
     const float2 I2[4] = {f2(1.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(1.f, 0.f)};
+    float gpsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // gradient mode, body tiles
 #pragma unroll
     for (int j = 0; j < NSLOT; j++) {
         if (!((mask >> j) & 1u)) continue;
@@ -788,18 +789,27 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
                 yo[0] = make_float4(Y[0].x, Y[0].y, Y[1].x, Y[1].y);
                 yo[1] = make_float4(Y[2].x, Y[2].y, Y[3].x, Y[3].y);
                 const int lp = pj, lq = U.diag ? qj : U.nr + qj;
-                if (P.grad_gains)
+                if (P.grad_gains) {
 #pragma unroll
-                for (int c = 0; c < 4; c++) {
-                    atomicAdd(&S.GG[lp * 8 + 2 * c], dGp[c].x);
-                    atomicAdd(&S.GG[lp * 8 + 2 * c + 1], dGp[c].y);
-                    atomicAdd(&S.GG[lq * 8 + 2 * c], dGq[c].x);
-                    atomicAdd(&S.GG[lq * 8 + 2 * c + 1], dGq[c].y);
+                    for (int c = 0; c < 4; c++) {
+                        if (role == 1) {        // body tile: one row antenna for every slot
+                            gpsum[2 * c] += dGp[c].x;
+                            gpsum[2 * c + 1] += dGp[c].y;
+                        } else {
+                            atomicAdd(&S.GG[lp * 8 + 2 * c], dGp[c].x);
+                            atomicAdd(&S.GG[lp * 8 + 2 * c + 1], dGp[c].y);
+                        }
+                        atomicAdd(&S.GG[lq * 8 + 2 * c], dGq[c].x);
+                        atomicAdd(&S.GG[lq * 8 + 2 * c + 1], dGq[c].y);
+                    }
                 }
             }
         }
     }
     if constexpr (GRAD) {
+        if (P.grad_gains && role == 1 && mask)
+#pragma unroll
+            for (int c = 0; c < 8; c++) atomicAdd(&S.GG[tl.p * 8 + c], gpsum[c]);
         __syncthreads();
         for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
             const int la = i >> 3;

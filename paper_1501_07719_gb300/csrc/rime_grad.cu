@@ -14,8 +14,10 @@
 //   c_uu, c_uv, c_vv = sum Re(g z beta) du^2, du dv, dv^2   (Gaussian shape)
 //   e_l, e_m = sum Re(g z beta) (dlnE_p + dlnE_q)             (beam with pointing errors)
 // and turns them into d/d(l, m, I, Q, U, V, alpha, major, minor, pa) with the
-// channel's and the source's factors. One partial per (t, k, unit) and
-// source is written; k_grad_reduce sums them in a fixed order.
+// channel's and the source's factors. A block loops over a group of
+// channels (the delays and the baseline table are staged once); one partial
+// per (t, channel group, unit) and source is written and k_colsum sums them
+// in a fixed order.
 #include "rime_internal.cuh"
 
 #include <algorithm>
@@ -32,21 +34,23 @@ constexpr int BLC = 128;        // baselines staged per step
 constexpr int GNLOC = 96;       // antennas of a unit, at most
 constexpr int NACC = 12;
 constexpr int NGRAD = 10;
+constexpr int NBMAX = 2048;     // baselines of a unit, at most (64 x 32 off-diagonal)
 
 template <typename T> struct GCfg;
 template <> struct GCfg<float> {
-    static constexpr int SG = 64;                 // sources per block
+    static constexpr int SG = 32;                 // sources per block
     using T2 = float2;
     using Chan = ChanF;
 };
 template <> struct GCfg<double> {
-    static constexpr int SG = 32;
+    static constexpr int SG = 16;
     using T2 = double2;
     using Chan = ChanD;
 };
 
 struct GradParams {
     int na, ntime, nchan, nsrc, nunits, nsch;
+    int chan_group, ncg;          // channels per block, channel groups
     long long nbl;
     int has_pointing;
     double ref_freq_hz;
@@ -61,6 +65,13 @@ struct GradParams {
     double *partials;
     const DevStatus *status;
 };
+
+__device__ __forceinline__ void cp16(void *smem, const void *gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ float round_i(float x) {
     const float M = 12582912.0f;
@@ -89,6 +100,11 @@ __device__ __forceinline__ double2 phase(const double *tau, long long i, const C
     sincospi(2.0 * r, &sn, &cs);
     return make_double2(cs, sn);
 }
+template <typename T> __device__ __forceinline__ T int_bits(int v);
+template <> __device__ __forceinline__ float int_bits<float>(int v) { return __int_as_float(v); }
+template <> __device__ __forceinline__ double int_bits<double>(int v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int bits_int(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int bits_int(double x) { return (int)__double_as_longlong(x); }
 __device__ __forceinline__ float gexp(float e) { return exp2f(e); }     // log2 units (FP32 coefficients)
 __device__ __forceinline__ double gexp(double e) { return exp(e); }     // natural units (FP64 coefficients)
 
@@ -126,17 +142,38 @@ __device__ __forceinline__ void beam_d(T cnu, T rho, T &E, T &t3) {
 }
 
 template <typename T>
+struct GSmem {
+    using T2 = typename GCfg<T>::T2;
+    using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+    static constexpr int SG = GCfg<T>::SG;
+    static size_t bytes(bool pointing) {
+        size_t b = (size_t)SG * GNLOC * (sizeof(TauT) + sizeof(T));   // raw delays and beam radii
+        b += (size_t)GNLOC * SG * sizeof(T2);                          // A
+        if (pointing) b += (size_t)GNLOC * SG * sizeof(T2);            // dlnE/dl, dlnE/dm
+        b += (size_t)NBMAX * 4 * sizeof(T);                            // baseline table
+        b += (size_t)2 * BLC * 4 * sizeof(T2);                         // Y chunks (double buffer)
+        return std::max(b, (size_t)GTHREADS * NGRAD * sizeof(double));
+    }
+};
+
+// One block: timestep t, a group of channels, one antenna unit, SG sources;
+// thread (source sl, baseline group grp).
+template <typename T>
 __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     using C = GCfg<T>;
     using T2 = typename C::T2;
     using Chan = typename C::Chan;
+    using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
     constexpr int SG = C::SG, NG = GTHREADS / SG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2 *sA = reinterpret_cast<T2 *>(smem_raw);                  // [GNLOC][SG]
-    T2 *sY = sA + GNLOC * SG;                                    // [BLC][4]
-    T *sB = reinterpret_cast<T *>(sY + BLC * 4);                // [BLC][4]: du, dv, dw, (p | q << 8)
-    T *sRed = sB + BLC * 4;                                      // [NG][SG][NACC]
-    T2 *sE = reinterpret_cast<T2 *>(sRed + NG * SG * NACC);      // [GNLOC][SG] dlnE/dl, dlnE/dm (pointing)
+    // layout: raw tau | raw rho | A | [dlnE] | baseline table | Y chunk
+    TauT *rTau = reinterpret_cast<TauT *>(smem_raw);
+    T *rRho = reinterpret_cast<T *>(rTau + SG * GNLOC);
+    T2 *sA = reinterpret_cast<T2 *>(rRho + SG * GNLOC);
+    T2 *sE = sA + GNLOC * SG;
+    T *sB = reinterpret_cast<T *>(P.has_pointing ? sE + GNLOC * SG : sE);
+    T2 *sY = reinterpret_cast<T2 *>(sB + 4 * NBMAX);
+    double *sRed = reinterpret_cast<double *>(smem_raw);   // reused at the end
 
     if (inputs_bad(P.status)) return;
     const int tid = threadIdx.x;
@@ -146,41 +183,39 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     bid /= P.nsch;
     const int u = bid % P.nunits;
     bid /= P.nunits;
-    const int k = bid % P.nchan;
-    const int t = bid / P.nchan;
+    const int cg = bid % P.ncg;
+    const int t = bid / P.ncg;
     const Unit U = P.units[u];
-    const Chan ch = reinterpret_cast<const Chan *>(P.chan)[k];
+    const int nb = U.nbody;
     const int s = sch * SG + sl;
     const bool sact = s < P.nsrc;
-    const int sidx = sact ? s : 0;
+    const int sidx = sact ? s : P.nsrc - 1;
     const int nloc = U.diag ? U.nr : U.nr + U.nc;
     const bool pointing = P.has_pointing != 0;
-    const T *extra = reinterpret_cast<const T *>(P.extra) + 8 * sidx;
-    const T l = extra[0], m = extra[1], l_n = extra[2], m_n = extra[3];
+    const int k0 = cg * P.chan_group, k1 = min(P.nchan, k0 + P.chan_group);
 
-    // ---- stage A (= K, or E K with pointing errors) for (antenna, source) ----
+    // ---- per block: delays of every (antenna, source) and the baseline table ----
     for (int i = tid; i < nloc * SG; i += GTHREADS) {
         const int a = i / SG, ss = i - a * SG;
         const int src = min(sch * SG + ss, P.nsrc - 1);
         const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
         const long long di = ((long long)t * P.nsrc + src) * P.na + ant;
-        using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
-        T2 v = phase(reinterpret_cast<const TauT *>(P.tau), di, ch);
-        if (pointing) {
-            // A = E K; dlnE/dl = t3 cnu^2 (l - dl_ta), dlnE/dm likewise (eq. 4)
-            const T rho = reinterpret_cast<const T *>(P.rho)[di];
-            const T *ex = reinterpret_cast<const T *>(P.extra) + 8 * src;
-            const double *pt = P.pointing + 2 * ((long long)t * P.na + ant);
-            T E, t3;
-            beam_d<T>(ch.cnu, rho, E, t3);
-            v.x *= E;
-            v.y *= E;
-            T2 d;
-            d.x = t3 * ch.cnu * ch.cnu * (ex[0] - (T)pt[0]);
-            d.y = t3 * ch.cnu * ch.cnu * (ex[1] - (T)pt[1]);
-            sE[a * SG + ss] = d;
-        }
-        sA[a * SG + ss] = v;
+        rTau[i] = reinterpret_cast<const TauT *>(P.tau)[di];
+        rRho[i] = reinterpret_cast<const T *>(P.rho)[di];
+    }
+    const uint16_t *bls = P.bls + U.tile0;
+    for (int i = tid; i < nb; i += GTHREADS) {
+        const uint16_t e = bls[i];
+        const int pl = e & 0xff, ql = e >> 8;
+        const int p = U.r0 + pl, q = U.c0 + ql;
+        const double *xp = P.uvw + 3 * ((long long)t * P.na + p);
+        const double *xq = P.uvw + 3 * ((long long)t * P.na + q);
+        const int la = pl, lb = U.diag ? ql : U.nr + ql;
+        T *b = sB + 4 * i;
+        b[0] = (T)(xp[0] - xq[0]);
+        b[1] = (T)(xp[1] - xq[1]);
+        b[2] = (T)(xp[2] - xq[2]);
+        b[3] = int_bits<T>((la * SG) | ((lb * SG) << 16));   // shared offsets of A_p, A_q
     }
 
     // ---- per-source constants of this thread ----
@@ -188,138 +223,183 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     const T sI = st[0], sQ = st[1], sU = st[2], sV = st[3];
     const T *gq = reinterpret_cast<const T *>(P.gauss) + 4 * sidx;
     const bool is_gauss = gq[3] != T(0);
-    const T gA = gq[0] * ch.nu2, gB = gq[1] * ch.nu2, gC = gq[2] * ch.nu2;
-
-    T acc[NACC];
-#pragma unroll
-    for (int i = 0; i < NACC; i++) acc[i] = T(0);
-
-    const uint16_t *bls = P.bls + U.tile0;
-    const int nb = U.nbody;
+    const T *extra = reinterpret_cast<const T *>(P.extra) + 8 * sidx;
+    const double l = extra[0], m = extra[1], l_n = extra[2], m_n = extra[3];
+    const double maj = extra[4], mn = extra[5], sp = extra[6], cp = extra[7];
+    const double alpha = (double)reinterpret_cast<const T *>(P.alpha)[sidx];
+    const double *ptab = pointing ? P.pointing + 2 * (long long)t * P.na : nullptr;
     const T2 *yin = reinterpret_cast<const T2 *>(P.yin);
-    for (int b0 = 0; b0 < nb; b0 += BLC) {
-        const int cnt = min(BLC, nb - b0);
-        __syncthreads();   // previous step done with sY / sB (and sA staged on the first)
-        for (int i = tid; i < cnt; i += GTHREADS) {
-            const uint16_t e = bls[b0 + i];
-            const int pl = e & 0xff, ql = e >> 8;
-            const int p = U.r0 + pl, q = U.c0 + ql;
-            const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
-            const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
+
+    double out[NGRAD];
 #pragma unroll
-            for (int c = 0; c < 4; c++) sY[4 * i + c] = yin[4 * row + c];
-            const double *xp = P.uvw + 3 * ((long long)t * P.na + p);
-            const double *xq = P.uvw + 3 * ((long long)t * P.na + q);
-            sB[4 * i + 0] = (T)(xp[0] - xq[0]);
-            sB[4 * i + 1] = (T)(xp[1] - xq[1]);
-            sB[4 * i + 2] = (T)(xp[2] - xq[2]);
-            const int la = pl, lb = U.diag ? ql : U.nr + ql;
-            sB[4 * i + 3] = (T)(la | (lb << 8));
+    for (int i = 0; i < NGRAD; i++) out[i] = 0.0;
+
+    // Y chunks of (channel, baseline chunk) in order, double-buffered: chunk j
+    // is prefetched while chunk j - 1 is summed.
+    const int nchunk = (nb + BLC - 1) / BLC;
+    auto issue_y = [&](int j) {
+        const int kk = k0 + j / nchunk, b0 = (j % nchunk) * BLC;
+        const int cnt = min(BLC, nb - b0);
+        T2 *dst = sY + (j & 1) * BLC * 4;
+        for (int i = tid; i < 2 * cnt; i += GTHREADS) {   // 2 x 16 bytes per baseline (FP32)
+            const int jj = i >> 1, half = i & 1;
+            const uint16_t e = bls[b0 + jj];
+            const int p = U.r0 + (e & 0xff), q = U.c0 + (e >> 8);
+            const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
+            const T2 *src = yin + 4 * (((long long)t * P.nbl + bl) * P.nchan + kk);
+            if (sizeof(T) == 4) {
+                cp16(dst + 4 * jj + 2 * half, src + 2 * half);
+            } else {
+                cp16(dst + 4 * jj + 2 * half, src + 2 * half);
+                cp16(dst + 4 * jj + 2 * half + 1, src + 2 * half + 1);
+            }
         }
-        __syncthreads();
-        for (int i = grp; i < cnt; i += NG) {
-            const T du = sB[4 * i], dv = sB[4 * i + 1], dw = sB[4 * i + 2];
-            const int pq = (int)sB[4 * i + 3];
-            const int la = pq & 0xff, lb = pq >> 8;
-            const T2 ap = sA[la * SG + sl], aq = sA[lb * SG + sl];
-            T zr = ap.x * aq.x + ap.y * aq.y;   // z = A_p conj(A_q)
-            T zi = ap.y * aq.x - ap.x * aq.y;
-            if (is_gauss) {
-                const T e = gA * du * du + gB * du * dv + gC * dv * dv;
-                const T g = gexp(e);
-                zr *= g;
-                zi *= g;
-            }
-            const T2 y0 = sY[4 * i], y1 = sY[4 * i + 1], y2 = sY[4 * i + 2], y3 = sY[4 * i + 3];
-            acc[0] += zr * y0.x - zi * y0.y;
-            acc[1] += zr * y1.x - zi * y1.y;
-            acc[2] += zr * y2.x - zi * y2.y;
-            acc[3] += zr * y3.x - zi * y3.y;
-            const T br = sI * y0.x + sQ * y1.x + sU * y2.x + sV * y3.x;
-            const T bi = sI * y0.y + sQ * y1.y + sU * y2.y + sV * y3.y;
-            const T re = zr * br - zi * bi, im = zr * bi + zi * br;   // z beta
-            acc[4] += im * du;
-            acc[5] += im * dv;
-            acc[6] += im * dw;
-            if (is_gauss) {
-                acc[7] += re * du * du;
-                acc[8] += re * du * dv;
-                acc[9] += re * dv * dv;
-            }
+        cp_commit();
+    };
+    const int njobs = (k1 - k0) * nchunk;
+    if (njobs > 0) issue_y(0);
+    int job = 0;
+    for (int k = k0; k < k1; k++) {
+        const Chan ch = reinterpret_cast<const Chan *>(P.chan)[k];
+        __syncthreads();   // delays staged / the previous channel is done with sA
+        // ---- A (= K, or E K with pointing errors) of every (antenna, source) ----
+        for (int i = tid; i < nloc * SG; i += GTHREADS) {
+            T2 v = phase(rTau + i, 0, ch);
             if (pointing) {
-                const T2 ep = sE[la * SG + sl], eq = sE[lb * SG + sl];
-                acc[10] += re * (ep.x + eq.x);
-                acc[11] += re * (ep.y + eq.y);
+                const int a = i / SG, ss = i - a * SG;
+                const int src = min(sch * SG + ss, P.nsrc - 1);
+                const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+                const T *ex = reinterpret_cast<const T *>(P.extra) + 8 * src;
+                T E, t3;
+                beam_d<T>(ch.cnu, rRho[i], E, t3);
+                v.x *= E;
+                v.y *= E;
+                T2 d;   // dlnE/dl, dlnE/dm = t3 cnu^2 (l - dl_ta, m - dm_ta)  (eq. 4)
+                d.x = t3 * ch.cnu * ch.cnu * (ex[0] - (T)ptab[2 * ant]);
+                d.y = t3 * ch.cnu * ch.cnu * (ex[1] - (T)ptab[2 * ant + 1]);
+                sE[i] = d;
             }
+            sA[i] = v;
+        }
+        const T gA = gq[0] * ch.nu2, gB = gq[1] * ch.nu2, gC = gq[2] * ch.nu2;
+        T acc[NACC];
+#pragma unroll
+        for (int i = 0; i < NACC; i++) acc[i] = T(0);
+        for (int b0 = 0; b0 < nb; b0 += BLC, job++) {
+            const int cnt = min(BLC, nb - b0);
+            cp_wait_all();
+            __syncthreads();   // chunk `job` landed; everyone is done with the other buffer
+            if (job + 1 < njobs) issue_y(job + 1);
+            const T2 *yb = sY + (job & 1) * BLC * 4;
+#pragma unroll 2
+            for (int i = grp; i < cnt; i += NG) {
+                const T *b = sB + 4 * (b0 + i);
+                const T du = b[0], dv = b[1], dw = b[2];
+                const int pq = bits_int(b[3]);
+                const int oa = pq & 0xffff, ob = pq >> 16;
+                const T2 ap = sA[oa + sl], aq = sA[ob + sl];
+                T zr = ap.x * aq.x + ap.y * aq.y;   // z = A_p conj(A_q)
+                T zi = ap.y * aq.x - ap.x * aq.y;
+                if (is_gauss) {
+                    const T g = gexp(gA * du * du + gB * du * dv + gC * dv * dv);
+                    zr *= g;
+                    zi *= g;
+                }
+                const T2 y0 = yb[4 * i], y1 = yb[4 * i + 1], y2 = yb[4 * i + 2], y3 = yb[4 * i + 3];
+                acc[0] += zr * y0.x - zi * y0.y;
+                acc[1] += zr * y1.x - zi * y1.y;
+                acc[2] += zr * y2.x - zi * y2.y;
+                acc[3] += zr * y3.x - zi * y3.y;
+                const T br = sI * y0.x + sQ * y1.x + sU * y2.x + sV * y3.x;
+                const T bi = sI * y0.y + sQ * y1.y + sU * y2.y + sV * y3.y;
+                const T re = zr * br - zi * bi, im = zr * bi + zi * br;   // z beta
+                acc[4] += im * du;
+                acc[5] += im * dv;
+                acc[6] += im * dw;
+                if (is_gauss) {
+                    acc[7] += re * du * du;
+                    acc[8] += re * du * dv;
+                    acc[9] += re * dv * dv;
+                }
+                if (pointing) {
+                    const T2 ep = sE[oa + sl], eq = sE[ob + sl];
+                    acc[10] += re * (ep.x + eq.x);
+                    acc[11] += re * (ep.y + eq.y);
+                }
+            }
+        }
+        // ---- this channel's factors (derivatives of eqs. 2-4), in the kernel's
+        // precision; the sums over channels are kept in FP64 ----
+        const T nu = nu_of<T>(ch);
+        const T lnr = log(nu / (T)P.ref_freq_hz);
+        T w = exp((T)alpha * lnr);              // spectral factor f
+        T dlnE2_l = 0, dlnE2_m = 0;
+        if (!pointing) {
+            T E, t3;                            // the beam E_s^2 shared by both antennas
+            beam_d<T>(ch.cnu, rRho[sl], E, t3);
+            w *= E * E;
+            const T cnu2 = ch.cnu * ch.cnu;
+            dlnE2_l = T(2) * t3 * cnu2 * (T)l;
+            dlnE2_m = T(2) * t3 * cnu2 * (T)m;
+        }
+        const T aR = sI * acc[0] + sQ * acc[1] + sU * acc[2] + sV * acc[3];
+        const T k2pi = T(2.0 * kPi / kCLight) * nu;
+        out[0] += (double)(w * (-k2pi * (acc[4] - (T)l_n * acc[6]) + (pointing ? acc[10] : aR * dlnE2_l)));
+        out[1] += (double)(w * (-k2pi * (acc[5] - (T)m_n * acc[6]) + (pointing ? acc[11] : aR * dlnE2_m)));
+        out[2] += (double)(w * acc[0]);
+        out[3] += (double)(w * acc[1]);
+        out[4] += (double)(w * acc[2]);
+        out[5] += (double)(w * acc[3]);
+        out[6] += (double)(w * aR * lnr);
+        if (is_gauss) {
+            // ln g = nu^2 (A du^2 + B du dv + C dv^2), A = -K (maj^2 sp^2 + min^2 cp^2),
+            // B = -2 K sp cp (maj^2 - min^2), C = -K (maj^2 cp^2 + min^2 sp^2), K = pi^2/(4 ln 2 c^2)
+            const T K = T(kGaussK / (kCLight * kCLight)) * nu * nu;
+            const T mj = (T)maj, mi = (T)mn, sps = (T)sp, cps = (T)cp;
+            const T dd = mj * mj - mi * mi;
+            const T Au = acc[7], Auv = acc[8], Av = acc[9];
+            out[7] += (double)(w * -K * (2 * mj * sps * sps * Au + 4 * mj * sps * cps * Auv + 2 * mj * cps * cps * Av));
+            out[8] += (double)(w * -K * (2 * mi * cps * cps * Au - 4 * mi * sps * cps * Auv + 2 * mi * sps * sps * Av));
+            out[9] += (double)(w * -K * (2 * sps * cps * dd * Au + 2 * dd * (cps * cps - sps * sps) * Auv -
+                                         2 * sps * cps * dd * Av));
         }
     }
-    // ---- combine the baseline groups, then the channel and source factors ----
+    // ---- combine the baseline groups in a fixed order: one partial per source ----
+    __syncthreads();
 #pragma unroll
-    for (int i = 0; i < NACC; i++) sRed[(grp * SG + sl) * NACC + i] = acc[i];
+    for (int i = 0; i < NGRAD; i++) sRed[(grp * SG + sl) * NGRAD + i] = out[i];
     __syncthreads();
     if (grp == 0 && sact) {
-        double a[NACC];
-        for (int i = 0; i < NACC; i++) {
-            double v = 0.0;
-            for (int g = 0; g < NG; g++) v += (double)sRed[(g * SG + sl) * NACC + i];
-            a[i] = v;
-        }
-        const double nu = (double)nu_of<T>(ch);
-        // spectral factor f = (nu/nu_ref)^alpha and, without pointing errors,
-        // the beam E_s^2 shared by both antennas
-        const double alpha = (double)reinterpret_cast<const T *>(P.alpha)[s];
-        const double lnr = log(nu / P.ref_freq_hz);
-        double w = exp(alpha * lnr);
-        double dlnE2_l = 0.0, dlnE2_m = 0.0;
-        if (!pointing) {
-            const T rho = reinterpret_cast<const T *>(P.rho)[((long long)t * P.nsrc + s) * P.na];
-            T E, t3;
-            beam_d<T>(ch.cnu, rho, E, t3);
-            w *= (double)E * (double)E;
-            const double cnu2 = (double)ch.cnu * (double)ch.cnu;
-            dlnE2_l = 2.0 * (double)t3 * cnu2 * (double)l;
-            dlnE2_m = 2.0 * (double)t3 * cnu2 * (double)m;
-        }
-        const double aR = (double)sI * a[0] + (double)sQ * a[1] + (double)sU * a[2] + (double)sV * a[3];
-        const double k2pi = 2.0 * 3.141592653589793 * nu / 299792458.0;
-        double out[NGRAD];
-        out[0] = w * (-k2pi * (a[4] - (double)l_n * a[6]) + (pointing ? a[10] : aR * dlnE2_l));
-        out[1] = w * (-k2pi * (a[5] - (double)m_n * a[6]) + (pointing ? a[11] : aR * dlnE2_m));
-        out[2] = w * a[0];
-        out[3] = w * a[1];
-        out[4] = w * a[2];
-        out[5] = w * a[3];
-        out[6] = w * aR * lnr;
-        out[7] = out[8] = out[9] = 0.0;
-        if (is_gauss) {
-            // ln g = nu^2 (A du^2 + B du dv + C dv^2) with
-            // A = -K (maj^2 sp^2 + min^2 cp^2), B = -K 2 sp cp (maj^2 - min^2),
-            // C = -K (maj^2 cp^2 + min^2 sp^2), K = pi^2 / (4 ln 2 c^2)
-            const double K = kGaussK / (kCLight * kCLight) * nu * nu;
-            const double maj = (double)extra[4], mn = (double)extra[5], sp = (double)extra[6], cp = (double)extra[7];
-            const double dd = maj * maj - mn * mn;
-            const double Au = a[7], Auv = a[8], Av = a[9];
-            out[7] = w * -K * (2 * maj * sp * sp * Au + 4 * maj * sp * cp * Auv + 2 * maj * cp * cp * Av);
-            out[8] = w * -K * (2 * mn * cp * cp * Au - 4 * mn * sp * cp * Auv + 2 * mn * sp * sp * Av);
-            out[9] = w * -K * (2 * sp * cp * dd * Au + 2 * dd * (cp * cp - sp * sp) * Auv - 2 * sp * cp * dd * Av);
-        }
-        const long long prow = (((long long)t * P.nchan + k) * P.nunits + u);
+        const long long prow = ((long long)t * P.ncg + cg) * P.nunits + u;
         double *o = P.partials + (prow * P.nsrc + s) * NGRAD;
-#pragma unroll
-        for (int i = 0; i < NGRAD; i++) o[i] = out[i];
+        for (int i = 0; i < NGRAD; i++) {
+            double v = 0.0;
+            for (int g = 0; g < NG; g++) v += sRed[(g * SG + sl) * NGRAD + i];
+            o[i] = v;
+        }
     }
 }
 
-// grad_src[s][j] = sum over (t, k, unit) of the partials, in index order.
-__global__ void k_grad_reduce(long long nrows, int nsrc, const double *partials, double *grad_src,
-                              const DevStatus *status) {
+// Column sums of a [nrows][ncols] array in fixed order: block (x, y) sums
+// rows [y rpb, (y+1) rpb) of 32 columns with 8 row phases, then the phases.
+constexpr int RTX = 32, RTY = 8;
+__global__ void k_colsum(long long nrows, long long ncols, long long rpb, const double *in, double *out,
+                         const DevStatus *status) {
+    __shared__ double red[RTY][RTX];
     if (inputs_bad(status)) return;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)nsrc * NGRAD;
-    if (i >= n) return;
+    const long long c = (long long)blockIdx.x * RTX + threadIdx.x;
+    const long long r0 = (long long)blockIdx.y * rpb;
+    const long long r1 = min(nrows, r0 + rpb);
     double acc = 0.0;
-    for (long long r = 0; r < nrows; r++) acc += partials[r * n + i];
-    grad_src[i] = acc;
+    if (c < ncols)
+        for (long long r = r0 + threadIdx.y; r < r1; r += RTY) acc += in[r * ncols + c];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < ncols) {
+        double v = 0.0;
+        for (int i = 0; i < RTY; i++) v += red[i][threadIdx.x];
+        out[(long long)blockIdx.y * ncols + c] = v;
+    }
 }
 
 }  // namespace
@@ -359,8 +439,13 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     const bool f64 = c->dims.precision == RIME_FP64;
     const int SG = f64 ? GCfg<double>::SG : GCfg<float>::SG;
     const int nsch = (c->nsrc + SG - 1) / SG;
-    const long long nrows = (long long)c->dims.ntime * c->dims.nchan * c->ngunits;
-    const size_t need = (size_t)nrows * c->nsrc * NGRAD;
+    const int chan_group = 8;
+    const int ncg = (c->dims.nchan + chan_group - 1) / chan_group;
+    const long long nrows = (long long)c->dims.ntime * ncg * c->ngunits;
+    const long long ncols = (long long)c->nsrc * NGRAD;
+    const long long rpb = 64;                    // rows per first-level block
+    const long long nrb = (nrows + rpb - 1) / rpb;
+    const size_t need = (size_t)(nrows + nrb) * ncols;
     if (need > c->gpart_cap) {
         if (c->d_gpart) cudaFree(c->d_gpart);
         c->d_gpart = nullptr;
@@ -376,6 +461,8 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     P.nsrc = c->nsrc;
     P.nunits = c->ngunits;
     P.nsch = nsch;
+    P.chan_group = chan_group;
+    P.ncg = ncg;
     P.nbl = c->nbl;
     P.has_pointing = c->has_pointing;
     P.ref_freq_hz = c->dims.ref_freq_hz;
@@ -394,25 +481,26 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     P.partials = c->d_gpart;
     P.status = c->d_status;
     const long long blocks = nrows * nsch;
-    const size_t ts = f64 ? 8 : 4;
-    const size_t t2 = 2 * ts;
-    size_t smem = (size_t)GNLOC * SG * t2 + (size_t)BLC * 4 * t2 + (size_t)BLC * 4 * ts +
-                  (size_t)(GTHREADS / SG) * SG * NACC * ts;
-    if (c->has_pointing) smem += (size_t)GNLOC * SG * t2;
     if (f64) {
+        const size_t smem = GSmem<double>::bytes(c->has_pointing);
         e = cudaFuncSetAttribute(k_grad_src<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_grad_src<double><<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     } else {
+        const size_t smem = GSmem<float>::bytes(c->has_pointing);
         e = cudaFuncSetAttribute(k_grad_src<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_grad_src<float><<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long n = (long long)c->nsrc * NGRAD;
-    k_grad_reduce<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(nrows, c->nsrc, c->d_gpart, grad_src,
-                                                                     c->d_status);
+    double *level1 = c->d_gpart + nrows * ncols;
+    const dim3 tb(RTX, RTY);
+    const unsigned gx = (unsigned)((ncols + RTX - 1) / RTX);
+    k_colsum<<<dim3(gx, (unsigned)nrb), tb, 0, c->stream>>>(nrows, ncols, rpb, c->d_gpart, level1, c->d_status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_colsum<<<dim3(gx, 1), tb, 0, c->stream>>>(nrb, ncols, nrb, level1, grad_src, c->d_status);
     return cudaGetLastError();
 }
 
