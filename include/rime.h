@@ -172,6 +172,74 @@ rime_status rime_ln_norm(rime_ctx *ctx, double *ln_norm);
  * status (failed input checks, kernel errors). */
 rime_status rime_sync(rime_ctx *ctx);
 
+/* Tensor-core modes of an RIME_FP32 context (rime_set_tensor_mode). */
+typedef enum {
+    RIME_TC_OFF = 0,          /* direct FP32 source sum (default) */
+    RIME_TC_SPLIT_BF16 = 1,   /* tcgen05 products of BF16 hi + lo operand pairs, FP32 accumulation */
+    RIME_TC_SPLIT_TF32 = 2    /* the same with TF32 hi + lo pairs (more accurate, half the rate) */
+} rime_tc_mode;
+
+/* Selects how rime_predict, rime_chi2 and rime_chi2_async evaluate the source
+ * sum of an RIME_FP32 context. With point sources the sum over s of
+ * A_ps X_s conj(A_qs), A = E K per antenna (eqs. 3-4), is a complex matrix
+ * product A diag(X) A^H for each (t, k) and Stokes X (the source sum of
+ * Algorithm 2 for all baselines at once); the split modes run it on the
+ * tensor cores with each operand split into a rounded high part and a
+ * rounded remainder (three products, FP32 accumulation). The phase nu tau is
+ * reduced exactly before its sine and cosine are taken with the SFU, and the
+ * chi^2 is summed in FP64. Typical error against the FP64 result: BF16
+ * about 1e-5 of the largest visibility, TF32 about 1e-6 (see the tests).
+ * The split modes take point sources only: a sky model with a Gaussian
+ * source makes the next waiting call return RIME_E_INVALID. rime_chi2_grad
+ * and rime_chi2_batched always use the direct FP32 path.
+ *   mode  a rime_tc_mode; RIME_E_INVALID for an RIME_FP64 context. */
+rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
+
+/* Configuration of the batched FP32 launch, and the autotuner's record.
+ * A work item of the persistent launch is (set, timestep, group of
+ * channels_per_item channels, antenna unit), each covering all of the set's
+ * sources; the grid holds blocks_per_sm blocks per SM. */
+typedef struct {
+    int32_t channels_per_item;  /* 1, 2 or 4 */
+    int32_t blocks_per_sm;      /* 1 or 2 */
+    int32_t order;              /* 0: largest sets first, 1: in set order */
+    int32_t tuned;              /* out: 1 if chosen by timing trials */
+    int32_t ntrials;            /* out: configurations timed, <= 16 */
+    int32_t trial_cfg[16][3];   /* out: (channels_per_item, blocks_per_sm, order) of each trial */
+    float trial_ms[16];         /* out: its time on the trial sample, ms */
+} rime_batch_config;
+
+/* chi^2 (eq. 7) of nsets sky models against the context's observation, data
+ * and gains: set j is sources src_offsets[j] .. src_offsets[j+1]-1 of `all`.
+ * The paper evaluates one sky model per solve of its BIRO loop (Fig. 3,
+ * Sec. 3); this entry point evaluates the many proposals of one sampler
+ * iteration in one persistent launch (FP32) or one launch per set (FP64).
+ *   nsets        >= 0 (0: nothing is computed)
+ *   src_offsets  HOST array [nsets + 1], src_offsets[0] = 0, non-decreasing,
+ *                src_offsets[nsets] = all->nsrc; empty sets are allowed
+ *   all          the concatenated sources, as for rime_set_sources (they
+ *                become the context's sources)
+ *   chi2_dev     device array [nsets] of double, receives chi^2 of each set
+ * Does not wait; suitable for CUDA graph capture once a first call with the
+ * same sizes has run outside capture (it allocates the buffers and, in FP32,
+ * times the candidate configurations on a sample of the work: the first
+ * timesteps, every set). Under capture the schedule is recorded into the
+ * graph as kernel arguments and the source arrays are re-read on each
+ * replay, so `all` must then be device memory updated in place. Each set's
+ * chi^2 is summed in a fixed order that does not depend on the
+ * configuration: results are reproducible run to run.
+ * Errors in source values are reported by the next call that waits. */
+rime_status rime_chi2_batched(rime_ctx *ctx, int32_t nsets, const int32_t *src_offsets,
+                              const rime_sources *all, double *chi2_dev);
+
+/* The configuration the last FP32 rime_chi2_batched call used (zeros before
+ * the first call). */
+rime_status rime_batched_config(const rime_ctx *ctx, rime_batch_config *out);
+
+/* Fixes the configuration of later batched calls (its first three fields;
+ * the rest is ignored); NULL returns to timing trials. */
+rime_status rime_set_batched_config(rime_ctx *ctx, const rime_batch_config *cfg);
+
 /* chi^2 for callers that cannot allocate device memory. The paper has no
  * counterpart to this call.
  *

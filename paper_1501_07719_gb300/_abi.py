@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "librime.so")
 
 RIME_OK, RIME_E_INVALID, RIME_E_STATE, RIME_E_OOM, RIME_E_CUDA, RIME_E_TIMEOUT, RIME_E_NONFINITE = range(7)
 RIME_FP32, RIME_FP64 = 0, 1
+RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 = 0, 1, 2
 
 
 class rime_dims(C.Structure):
@@ -26,6 +27,12 @@ class rime_dims(C.Structure):
 class rime_sources(C.Structure):
     _fields_ = [("nsrc", C.c_int32), ("time_varying", C.c_int32), ("lm", C.c_void_p),
                 ("stokes", C.c_void_p), ("alpha", C.c_void_p), ("shape", C.c_void_p)]
+
+
+class rime_batch_config(C.Structure):
+    _fields_ = [("channels_per_item", C.c_int32), ("blocks_per_sm", C.c_int32), ("order", C.c_int32),
+                ("tuned", C.c_int32), ("ntrials", C.c_int32), ("trial_cfg", (C.c_int32 * 3) * 16),
+                ("trial_ms", C.c_float * 16)]
 
 
 class RimeError(RuntimeError):
@@ -64,6 +71,12 @@ def lib():
         L.rime_chi2_noalloc.argtypes = [C.POINTER(rime_dims), vp, vp, vp, vp, vp, vp,
                                         C.POINTER(rime_sources), vp, vp]
         L.rime_chi2_noalloc.restype = ip
+        L.rime_chi2_batched.argtypes = [vp, C.c_int32, vp, C.POINTER(rime_sources), vp]
+        L.rime_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
+        L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
+        L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
+        for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode"):
+            getattr(L, f).restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
                   "rime_ln_norm", "rime_sync"):
@@ -239,3 +252,39 @@ def rime_chi2_noalloc(na, ntime, nchan, precision, freq_hz, uvw, pointing, data,
                                 k.ptr(gains, np.complex128, "gains"), C.byref(src),
                                 chi2_dev.data_ptr(), stream or None)
     _check(s, None)
+
+
+def rime_chi2_batched(ctx, src_offsets, lm, stokes, alpha, shape, chi2_dev):
+    """chi^2 of each source set against the context's observation.
+    src_offsets: host int32 [nsets + 1]; the source arrays hold the
+    concatenated sets; chi2_dev: float64 device tensor [nsets]."""
+    off = np.ascontiguousarray(src_offsets, dtype=np.int32)
+    nsets = int(off.shape[0]) - 1
+    k = _Keep()
+    src = make_sources(lm, stokes, alpha, shape, k)
+    out = chi2_dev.data_ptr() if chi2_dev is not None and nsets > 0 else None
+    _check(lib().rime_chi2_batched(ctx, nsets, off.ctypes.data, C.byref(src), out), ctx)
+
+
+def rime_batched_config(ctx) -> dict:
+    """The batched launch configuration in use and the tuner's trials."""
+    c = rime_batch_config()
+    _check(lib().rime_batched_config(ctx, C.byref(c)), ctx)
+    trials = [dict(channels_per_item=c.trial_cfg[i][0], blocks_per_sm=c.trial_cfg[i][1],
+                   order=c.trial_cfg[i][2], ms=float(c.trial_ms[i])) for i in range(c.ntrials)]
+    return dict(channels_per_item=c.channels_per_item, blocks_per_sm=c.blocks_per_sm, order=c.order,
+                tuned=bool(c.tuned), trials=trials)
+
+
+def rime_set_batched_config(ctx, channels_per_item=None, blocks_per_sm=2, order=0):
+    """Fixes the batched configuration; channels_per_item=None returns to tuning."""
+    if channels_per_item is None:
+        _check(lib().rime_set_batched_config(ctx, None), ctx)
+        return
+    c = rime_batch_config(channels_per_item, blocks_per_sm, order)
+    _check(lib().rime_set_batched_config(ctx, C.byref(c)), ctx)
+
+
+def rime_set_tensor_mode(ctx, mode: int):
+    """RIME_TC_OFF, RIME_TC_SPLIT_BF16 or RIME_TC_SPLIT_TF32 (FP32 contexts)."""
+    _check(lib().rime_set_tensor_mode(ctx, int(mode)), ctx)

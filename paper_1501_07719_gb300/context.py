@@ -71,6 +71,28 @@ class Rime:
         chi = A.rime_chi2_grad(self.ctx, gs, gg)
         return chi, gs, gg
 
+    def chi2_batched(self, offsets, sources: dict, out=None):
+        """chi^2 of each source set (set j = sources offsets[j]:offsets[j+1])
+        as a float64 device tensor [nsets]; does not wait."""
+        nsets = len(offsets) - 1
+        if out is None:
+            out = self.torch.empty(max(nsets, 0), dtype=self.torch.float64, device="cuda")
+        A.rime_chi2_batched(self.ctx, offsets, sources["lm"], sources["stokes"], sources["alpha"],
+                            sources.get("shape"), out)
+        self.nsrc = int(sources["alpha"].shape[0])
+        return out
+
+    def set_tensor_mode(self, mode: int):
+        """Tensor-core split-precision source sum for point sources
+        (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32) or the direct sum (RIME_TC_OFF)."""
+        A.rime_set_tensor_mode(self.ctx, mode)
+
+    def batched_config(self) -> dict:
+        return A.rime_batched_config(self.ctx)
+
+    def set_batched_config(self, channels_per_item=None, blocks_per_sm=2, order=0):
+        A.rime_set_batched_config(self.ctx, channels_per_item, blocks_per_sm, order)
+
     def ln_norm(self) -> float:
         return A.rime_ln_norm(self.ctx)
 

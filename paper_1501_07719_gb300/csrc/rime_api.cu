@@ -19,6 +19,13 @@ void build_units(int na, int precision, std::vector<Unit> &units, std::vector<Ti
 
 using namespace rime;
 
+namespace rime {
+size_t alloc_cap() {
+    const char *s = std::getenv("RIME_TEST_MAX_BYTES");
+    return s ? (size_t)std::strtoull(s, nullptr, 10) : (size_t)-1;
+}
+}  // namespace rime
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -45,30 +52,20 @@ rime_status cuda_fail(rime_ctx *c, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-// Test hook: RIME_TEST_MAX_BYTES caps the device memory one context may
-// allocate, so that the out-of-memory path can be exercised.
-size_t alloc_cap() {
-    const char *s = std::getenv("RIME_TEST_MAX_BYTES");
-    return s ? (size_t)std::strtoull(s, nullptr, 10) : (size_t)-1;
-}
+}  // namespace
 
-struct Alloc {
-    rime_ctx *c;
-    size_t total = 0, cap = alloc_cap();
-    cudaError_t operator()(void **p, size_t bytes) {
-        if (bytes == 0) bytes = 16;
-        if (total + bytes > cap) return cudaErrorMemoryAllocation;
-        total += bytes;
-        return cudaMalloc(p, bytes);
-    }
-};
+rime_status rime::fail_ctx(rime_ctx *c, rime_status s, const std::string &msg) { return fail(c, s, msg); }
+rime_status rime::cuda_fail_ctx(rime_ctx *c, cudaError_t e, const char *what) { return cuda_fail(c, e, what); }
+
+namespace {
 
 void free_all(rime_ctx *c) {
     void *ptrs[] = {c->d_freq, c->d_chan, c->d_uvw, c->d_uvw_f, c->d_pointing, c->d_data,
                     c->d_weight, c->d_gains_in, c->d_gains, c->d_src_in, c->d_stokes,
                     c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho, c->d_units,
                     c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
-                    c->d_gunits, c->d_gbl};
+                    c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
+                    c->d_spart, c->d_scounter, c->d_sscale};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_status) cudaFreeHost(c->h_status);
@@ -93,6 +90,12 @@ cudaError_t reset_class(rime_ctx *c, int cls) {
     return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t rime::reset_status_class(rime_ctx *c, int cls) { return reset_class(c, cls); }
+
+namespace {
+
 const char *class_name(int cls) {
     switch (cls) {
         case EC_FREQ: return "freq_hz";
@@ -100,6 +103,7 @@ const char *class_name(int cls) {
         case EC_DATA: return "data/weight";
         case EC_GAINS: return "gains";
         case EC_SRC: return "sources";
+        case EC_MODE: return "sources (tensor-core mode)";
         default: return "kernel";
     }
 }
@@ -114,6 +118,16 @@ rime_status sync_status(rime_ctx *c) {
         if (!e) continue;
         char buf[256];
         long long idx = c->h_status->first_bad[cls];
+        if (cls == EC_RUN) {
+            CK(c, reset_class(c, EC_RUN), "reset status");
+            return fail(c, RIME_E_TIMEOUT, "a kernel gave up a bounded wait (pipeline stalled)");
+        }
+        if (cls == EC_MODE) {
+            std::snprintf(buf, sizeof buf,
+                          "the split-precision tensor-core mode takes point sources only "
+                          "(first Gaussian source: %lld); use RIME_TC_OFF", idx);
+            return fail(c, RIME_E_INVALID, buf);
+        }
         if (e & EB_NONFINITE) {
             std::snprintf(buf, sizeof buf, "%s: NaN or Inf (first at element %lld)", class_name(cls), idx);
             return fail(c, RIME_E_NONFINITE, buf);
@@ -352,6 +366,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
                                   c->stream), "copying shape");
     }
     CK(c, reset_class(c, EC_SRC), "reset status");
+    CK(c, reset_class(c, EC_MODE), "reset status");
     c->sources_set = true;
     CK(c, launch_prep_sources(c), "source factors");
     return RIME_OK;
@@ -361,7 +376,8 @@ rime_status rime_predict(rime_ctx *c, void *vis_out) {
     if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
     if (!vis_out) return fail(c, RIME_E_INVALID, "vis_out is NULL");
     if (!c->sources_set) return fail(c, RIME_E_STATE, "rime_set_sources has not been called");
-    CK(c, launch_fused(c, vis_out, nullptr, false), "predict kernel");
+    if (c->tc_mode != RIME_TC_OFF) CK(c, launch_split(c, true, vis_out, nullptr), "tensor-core predict kernel");
+    else CK(c, launch_fused(c, vis_out, nullptr, false), "predict kernel");
     return RIME_OK;
 }
 
@@ -370,7 +386,19 @@ rime_status rime_chi2_async(rime_ctx *c, double *chi2_dev) {
     if (!chi2_dev) return fail(c, RIME_E_INVALID, "chi2_dev is NULL");
     if (!c->sources_set) return fail(c, RIME_E_STATE, "rime_set_sources has not been called");
     if (!c->has_data) return fail(c, RIME_E_STATE, "no observed data (rime_set_data)");
-    CK(c, launch_fused(c, nullptr, chi2_dev, true), "chi2 kernel");
+    if (c->tc_mode != RIME_TC_OFF) CK(c, launch_split(c, false, nullptr, chi2_dev), "tensor-core chi2 kernel");
+    else CK(c, launch_fused(c, nullptr, chi2_dev, true), "chi2 kernel");
+    return RIME_OK;
+}
+
+rime_status rime_set_tensor_mode(rime_ctx *c, int32_t mode) {
+    if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
+    if (mode != RIME_TC_OFF && mode != RIME_TC_SPLIT_BF16 && mode != RIME_TC_SPLIT_TF32)
+        return fail(c, RIME_E_INVALID, "mode must be RIME_TC_OFF, RIME_TC_SPLIT_BF16 or RIME_TC_SPLIT_TF32");
+    if (mode != RIME_TC_OFF && c->dims.precision != RIME_FP32)
+        return fail(c, RIME_E_INVALID, "the tensor-core modes need an RIME_FP32 context");
+    c->tc_mode = mode;
+    CK(c, reset_class(c, EC_MODE), "reset status");
     return RIME_OK;
 }
 

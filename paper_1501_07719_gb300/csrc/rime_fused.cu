@@ -26,6 +26,7 @@
 // error before sincospi; the FP64 delays come from the upload kernels, so the
 // kernel issues no FP64 instruction outside the final reduction.
 #include "rime_internal.cuh"
+#include "rime_dev.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -35,16 +36,6 @@ namespace rime {
 // ===========================================================================
 // Shared device helpers
 // ===========================================================================
-__device__ __forceinline__ float round_int_f(float x) {
-    // nearest integer for |x| < 2^22 (1.5 * 2^23 magic constant), ties to even
-    const float M = 12582912.0f;
-    return __fsub_rn(__fadd_rn(x, M), M);
-}
-__device__ __forceinline__ double round_int_d(double x) {
-    const double M = 6755399441055744.0;   // 1.5 * 2^52
-    return __dsub_rn(__dadd_rn(x, M), M);
-}
-
 __device__ __forceinline__ float ex2_approx(float e) {
     float g;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
@@ -106,31 +97,6 @@ __device__ void finish_chi2(double block_value, const FusedParams &P, double *re
             *P.counter = 0u;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// 2x2 complex matrices (row-major 00, 01, 10, 11) for the epilogues
-// ---------------------------------------------------------------------------
-template <typename T2> __device__ __forceinline__ T2 cmk(double x, double y);
-template <> __device__ __forceinline__ float2 cmk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
-template <> __device__ __forceinline__ double2 cmk<double2>(double x, double y) { return make_double2(x, y); }
-template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
-    T2 r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
-}
-template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {   // a conj(b)
-    T2 r; r.x = a.x * b.x + a.y * b.y; r.y = a.y * b.x - a.x * b.y; return r;
-}
-template <typename T2> __device__ __forceinline__ T2 cadd(T2 a, T2 b) { T2 r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
-template <typename T2> __device__ __forceinline__ T2 csub(T2 a, T2 b) { T2 r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
-template <typename T2> __device__ __forceinline__ T2 cconj(T2 a) { T2 r; r.x = a.x; r.y = -a.y; return r; }
-template <typename T2> __device__ __forceinline__ void mmul(const T2 *a, const T2 *b, T2 *o) {
-    T2 r0 = cadd(cmul(a[0], b[0]), cmul(a[1], b[2])), r1 = cadd(cmul(a[0], b[1]), cmul(a[1], b[3]));
-    T2 r2 = cadd(cmul(a[2], b[0]), cmul(a[3], b[2])), r3 = cadd(cmul(a[2], b[1]), cmul(a[3], b[3]));
-    o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3;
-}
-template <typename T2> __device__ __forceinline__ void mherm(const T2 *a, T2 *o) {
-    T2 r1 = cconj(a[2]), r2 = cconj(a[1]);
-    o[0] = cconj(a[0]); o[1] = r1; o[2] = r2; o[3] = cconj(a[3]);
 }
 
 // Adjoint of the chi^2 term of one visibility (eq. 7 through eq. 1):
@@ -261,8 +227,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     const double *stokes = reinterpret_cast<const double *>(P.stokes) + (long long)t * P.stokes_tstride;
     const double *alpha = reinterpret_cast<const double *>(P.alpha);
 
-    for (int s0 = 0; s0 < P.nsrc; s0 += SC) {
-        const int sc = min(SC, P.nsrc - s0);
+    for (int s0 = P.src0; s0 < P.src1; s0 += SC) {
+        const int sc = min(SC, P.src1 - s0);
         for (int j = tid; j < sc * nloc; j += THREADS) {
             int s = j / nloc, a = j - s * nloc;
             int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
@@ -513,19 +479,12 @@ __device__ __forceinline__ float2 gauss2(float2 qp, float2 up, float2 vp, float2
     return f2(ex2_approx(e.x), ex2_approx(e.y));
 }
 
+// One work item: timestep t, channel k, antenna unit u, sources [sb, se).
+// Returns the block's chi^2 (in thread 0; chi^2 modes only).
 template <int MODE>
-__global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
+__device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se) {
     constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
-    __shared__ int sLast;
-
-    if (inputs_bad(P.status)) return;
     const int tid = threadIdx.x;
-    const int u = blockIdx.x % P.nunits;
-    const int rest = blockIdx.x / P.nunits;
-    const int k = rest % P.nchan;
-    const int t = rest / P.nchan;
     const Unit U = P.units[u];
     const ChanF ch = reinterpret_cast<const ChanF *>(P.chan)[k];
     const int nloc = U.diag ? U.nr : U.nr + U.nc;
@@ -540,7 +499,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
 
     // prefetch of one chunk's per-(s, a) delays and per-source constants
     auto issue = [&](int s0) {
-        const int sc = min(SC, P.nsrc - s0);
+        const int sc = min(SC, se - s0);
         for (int s = it_s0, a = it_a0; s < sc;) {
             int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
             long long di = ((long long)t * P.nsrc + s0 + s) * P.na + ant;
@@ -557,7 +516,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
         }
         cp_async_commit();
     };
-    if (P.nsrc > 0) issue(0);
+    if (se > sb) issue(sb);
     for (int a = tid; a < nloc; a += THREADS) {
         int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
         float4 x = P.uvw_f[(long long)t * P.na + ant];
@@ -600,8 +559,8 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
 
-    for (int s0 = 0; s0 < P.nsrc; s0 += SC) {
-        const int sc = min(SC, P.nsrc - s0);
+    for (int s0 = sb; s0 < se; s0 += SC) {
+        const int sc = min(SC, se - s0);
         cp_async_wait_all();
         __syncthreads();
         // ---- stage the per-antenna factors of the chunk (Algorithm 1) ----
@@ -645,7 +604,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
             S.Gf[tid] = S.rG[tid].w;
         }
         __syncthreads();
-        if (s0 + SC < P.nsrc) issue(s0 + SC);
+        if (s0 + SC < se) issue(s0 + SC);
 
         // ---- source sum for this thread's baselines (Algorithm 2) ----
         if (role == 1) {
@@ -817,16 +776,75 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
             atomicAdd(&P.grad_gains[8 * (((long long)t * P.na + ant) * P.nchan + k) + (i & 7)], (double)S.GG[i]);
         }
     }
+    double bsum = 0.0;
     if constexpr (CHI2) {
-        // thread and warp sums in FP32 (positive terms), block and grid in FP64
+        // thread and warp sums in FP32 (positive terms), block in FP64
         float w = chi;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-        double bsum = block_sum<THREADS>((threadIdx.x & 31) == 0 ? (double)w : 0.0, S.red);
-        finish_chi2<THREADS>(bsum, P, S.red, &sLast);
+        bsum = block_sum<THREADS>((threadIdx.x & 31) == 0 ? (double)w : 0.0, S.red);
+    }
+    return bsum;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int sLast;
+    if (inputs_bad(P.status)) return;
+    const int u = blockIdx.x % P.nunits;
+    const int rest = blockIdx.x / P.nunits;
+    const int k = rest % P.nchan;
+    const int t = rest / P.nchan;
+    const double bsum = fused_item<MODE>(P, S, t, k, u, 0, P.nsrc);
+    if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
+}
+
+// Batched chi^2: many source sets against one observation in one persistent
+// launch. A work item is (set rank, t, channel group, unit); blocks take
+// items from a counter (ranks in the order given, largest sets first by
+// default) and store one partial per (set, t, channel, unit), so the sums do
+// not depend on the schedule.
+__global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(const FusedParams P, const BatchParams B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ long long sItem;
+    if (inputs_bad(P.status)) return;
+    for (;;) {
+        __syncthreads();   // the previous item is done with the shared buffers
+        if (threadIdx.x == 0) sItem = (long long)atomicAdd(B.counter, 1ull);
+        __syncthreads();
+        const long long item = sItem;
+        if (item >= B.nitems) break;
+        const int rank = (int)(item / B.items_per_set);
+        const int w = (int)(item - (long long)rank * B.items_per_set);
+        const int j = B.order[rank];
+        const int u = w % P.nunits;
+        const int rest = w / P.nunits;
+        const int kc = rest % B.nkc;
+        const int t = rest / B.nkc;
+        const int k1 = min(P.nchan, (kc + 1) * B.cpi);
+        for (int k = kc * B.cpi; k < k1; k++) {
+            const double bsum = fused_item<MODE_CHI2>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
+            if (threadIdx.x == 0)
+                B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
+            __syncthreads();
+        }
     }
 }
 }  // namespace f32
+
+// chi2[j] = sum of set j's per-item partials, in index order.
+__global__ void k_set_sums(int per_set, const double *partials, double *chi2, const DevStatus *status) {
+    __shared__ double red[32];
+    if (inputs_bad(status)) return;
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < per_set; i += 256) acc += partials[(long long)j * per_set + i];
+    const double tot = block_sum<256>(acc, red);
+    if (threadIdx.x == 0) chi2[j] = tot;
+}
 
 // ===========================================================================
 // Host side: work units and launch
@@ -934,9 +952,8 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
     return launch_fused_mode(c, chi2 ? MODE_CHI2 : MODE_PREDICT, vis_out, result, nullptr, nullptr);
 }
 
-cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
-                              double *grad_gains) {
-    FusedParams P{};
+static void fill_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
+                        double *grad_gains) {
     P.na = c->dims.na;
     P.ntime = c->dims.ntime;
     P.nchan = c->dims.nchan;
@@ -968,6 +985,14 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
     P.status = c->d_status;
     P.yout = yout;
     P.grad_gains = grad_gains;
+    P.src0 = 0;
+    P.src1 = c->nsrc;
+}
+
+cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
+                              double *grad_gains) {
+    FusedParams P{};
+    fill_params(c, P, vis_out, result, yout, grad_gains);
     int blocks = fused_blocks(c);
     if (blocks == 0) return cudaSuccess;
     if (c->dims.precision == RIME_FP64) {
@@ -984,6 +1009,44 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
         case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2>, P, blocks, f32::THREADS, sm, c->stream);
         default: return launch_k(f32::k_fused_f32<MODE_GRAD>, P, blocks, f32::THREADS, sm, c->stream);
     }
+}
+
+cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid) {
+    FusedParams P{};
+    fill_params(c, P, nullptr, nullptr, nullptr, nullptr);
+    if (grid <= 0 || B.nitems == 0) return cudaSuccess;
+    const size_t sm = sizeof(f32::Smem);
+    cudaError_t e = cudaFuncSetAttribute(f32::k_batched_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    f32::k_batched_f32<<<grid, f32::THREADS, sm, c->stream>>>(P, B);
+    return cudaGetLastError();
+}
+
+int batched_blocks_per_sm() {
+    int n = 0;
+    if (cudaFuncSetAttribute(f32::k_batched_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(f32::Smem)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32::k_batched_f32, f32::THREADS, sizeof(f32::Smem)) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *partials, double *chi2) {
+    if (nsets <= 0) return cudaSuccess;
+    k_set_sums<<<nsets, 256, 0, c->stream>>>(per_set, partials, chi2, c->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result) {
+    FusedParams P{};
+    fill_params(c, P, nullptr, result, nullptr, nullptr);
+    P.src0 = src0;
+    P.src1 = src1;
+    const int blocks = fused_blocks(c);
+    if (blocks == 0) return cudaSuccess;
+    return launch_k(f64::k_fused_f64<MODE_CHI2>, P, blocks, f64::THREADS, f64::smem_bytes(), c->stream);
 }
 
 }  // namespace rime

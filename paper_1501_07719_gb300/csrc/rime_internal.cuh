@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/rime.h"
 
@@ -32,10 +33,13 @@ constexpr double kLog2e = 1.4426950408889634;
 
 // Error classes: one status word per input class, cleared when that input
 // is set again.
-enum ErrClass { EC_FREQ = 0, EC_UVW = 1, EC_DATA = 2, EC_GAINS = 3, EC_SRC = 4, EC_RUN = 5, EC_N = 8 };
+// EC_RUN: a kernel gave up a bounded wait (reported once, then cleared);
+// EC_MODE: the sources do not suit the tensor-core mode (Gaussian sources).
+enum ErrClass { EC_FREQ = 0, EC_UVW = 1, EC_DATA = 2, EC_GAINS = 3, EC_SRC = 4, EC_RUN = 5, EC_MODE = 6, EC_N = 8 };
 enum ErrBits : int {
     EB_NONFINITE = 1,
     EB_RANGE = 2,       // value outside its domain (l^2+m^2 >= 1, w < 0, nu <= 0, axes)
+    EB_TIMEOUT = 4,     // a bounded wait inside a kernel gave up
 };
 
 // Status block in device memory, copied to the host in one transfer.
@@ -110,6 +114,20 @@ struct FusedParams {
     // gradient mode only
     void *yout;                // complex T [ntime][nbl][nchan][4]: Stokes-projected adjoint Y_X
     double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
+    int src0, src1;            // FP64 kernel: the source range [src0, src1) of this launch
+};
+
+// Batched chi^2: the schedule of a persistent launch. Work item i is
+// (rank, t, channel group, unit) with rank = i / items_per_set.
+struct BatchParams {
+    long long nitems;          // ranks * items_per_set (fewer ranks or timesteps in a tuning trial)
+    int items_per_set;         // timesteps covered * nkc * nunits
+    int per_set;               // partials per set: ntime * nchan * nunits
+    int nkc, cpi;              // channel groups, channels per group
+    const int *order;          // set of each rank
+    const int *offsets;        // [nsets + 1] source offsets
+    unsigned long long *counter;   // next work item (zeroed before the launch)
+    double *partials;          // [nsets][ntime][nchan][nunits]
 };
 
 // Kernel modes of the fused predict / chi^2 kernels.
@@ -120,7 +138,7 @@ __device__ __forceinline__ bool inputs_bad(const DevStatus *st) {
     int e = 0;
 #pragma unroll
     for (int i = 0; i < EC_RUN; i++) e |= st->err[i];
-    return e != 0;
+    return (e | st->err[EC_MODE]) != 0;
 }
 
 }  // namespace rime
@@ -177,6 +195,30 @@ struct rime_ctx {
     unsigned int *d_counter = nullptr;
     rime::DevStatus *d_status = nullptr;
     rime::DevStatus *h_status = nullptr;   // pinned
+    // batched chi^2 (allocated by the first rime_chi2_batched)
+    int *d_bsched = nullptr;          // [order by size (cap) | set order (cap) | offsets (cap + 1)]
+    size_t bsched_cap = 0;            // sets
+    double *d_bpart = nullptr;        // per (set, t, k, unit) partials
+    size_t bpart_cap = 0;
+    unsigned long long *d_bcounter = nullptr;
+    rime_batch_config bcfg{};         // configuration of the last FP32 batched call
+    bool bcfg_forced = false;
+    struct BatchTune {
+        int nsets, nsrc;
+        rime_batch_config cfg;
+    };
+    std::vector<BatchTune> btuned;    // tuned configurations by (nsets, total sources)
+    int bmax_bps = 0;                 // resident batched blocks per SM (0: not queried yet)
+    int nsm = 0;
+    // tensor-core split-precision mode (FP32 contexts)
+    int tc_mode = 0;                  // rime_tc_mode
+    int2 *d_stiles = nullptr;         // its tiles (p0, q0)
+    int nstiles = 0;
+    double *d_spart = nullptr;        // one partial chi^2 per block
+    size_t spart_cap = 0;
+    unsigned *d_scounter = nullptr;
+    void *d_sscale = nullptr;         // per (t, k, source) Stokes scale factors
+    size_t sscale_cap = 0;
 
     size_t tsize() const { return dims.precision == RIME_FP64 ? 8 : 4; }
 };
@@ -199,6 +241,31 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
 int fused_blocks(const rime_ctx *c);
 int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
                       int *ntiles);
+cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid);
+int batched_blocks_per_sm();
+cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *partials, double *chi2);
+cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result);
+// rime_split.cu
+cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result);
+// rime_api.cu: clears one error class of the status block (stream-ordered)
+cudaError_t reset_status_class(rime_ctx *c, int cls);
 // sets the message rime_last_error(NULL) returns (rime_api.cu)
 void set_global_error(const char *msg);
+// error reporting and the allocation cap shared by the entry points (rime_api.cu)
+rime_status fail_ctx(rime_ctx *c, rime_status s, const std::string &msg);
+rime_status cuda_fail_ctx(rime_ctx *c, cudaError_t e, const char *what);
+size_t alloc_cap();
+
+// Device allocations of one context call; RIME_TEST_MAX_BYTES caps their sum,
+// so that the out-of-memory path can be exercised.
+struct Alloc {
+    rime_ctx *c;
+    size_t total = 0, cap = alloc_cap();
+    cudaError_t operator()(void **p, size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        if (total + bytes > cap) return cudaErrorMemoryAllocation;
+        total += bytes;
+        return cudaMalloc(p, bytes);
+    }
+};
 }  // namespace rime

@@ -1,0 +1,599 @@
+// rime_split.cu -- the RIME predict / chi^2 of point sources on the tcgen05
+// tensor cores, in split precision.
+//
+// With point sources the per-baseline source sum factors through the
+// per-antenna terms A_tpsk = E_tpsk K_tpsk (eqs. 3-4): for each (t, k) and
+// each Stokes parameter X in (I, Q, U, V),
+//
+//   S_X[p, q] = sum_s A_ps X_s conj(A_qs)  =  (A diag(X) A^H)[p, q],
+//
+// a complex matrix product over the sources (the sum of Algorithm 2 for all
+// baselines at once). With the source index and the real/imaginary part as
+// the contraction index (K = 2 nsrc) it is two real products,
+//
+//   Re S_X[p, q] = sum_s [Re A_ps, Im A_ps] . X_s [Re A_qs, Im A_qs]
+//   Im S_X[p, q] = sum_s [Im A_ps, -Re A_ps] . X_s [Re A_qs, Im A_qs],
+//
+// which the tensor cores evaluate in FP32 from operands split into a high
+// and a low part (x = hi + lo, hi = x rounded to BF16 or TF32, lo = the
+// rounded remainder): x y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y, three MMAs
+// per product; the lo_x lo_y term (relative 2^-16 for BF16, 2^-22 for TF32)
+// is dropped.
+//
+// One CTA owns (t, k) and a tile of 128 row antennas p (the MMA's M, one
+// TMEM lane each) by 64 column antennas q; the B operand has one row per
+// (q, X), N = 256, and the two accumulators (Re and Im parts, 256 FP32
+// columns each) fill the SM's 512 TMEM columns. Eight producer warps form
+// the operands of each chunk of sources straight into shared memory: the
+// phase nu tau is reduced exactly in double-float arithmetic (the delays
+// tau come from the FP64 upload kernel) and its sine and cosine are taken
+// with the SFU; one thread issues the MMAs; a six-stage mbarrier pipeline
+// connects them. The epilogue reads the accumulators from TMEM, applies the
+// Stokes combination (eq. 2) and the gains (eq. 1), and writes V or forms
+// w |V - D|^2 (eq. 7), summed in FP64.
+#include "rime_internal.cuh"
+#include "rime_dev.cuh"
+#include "rime_tc.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace rime {
+namespace split {
+
+constexpr int PT = 128;                 // row antennas per tile (MMA M)
+constexpr int QT = 64;                  // column antennas per tile
+constexpr int NB = 4 * QT;              // B rows: (q, X), MMA N
+constexpr int NPROD = 256;              // producer / epilogue threads
+constexpr int THREADS = NPROD + 32;     // and one MMA warp
+constexpr int NST = 6;                  // pipeline stages
+constexpr uint32_t A_BYTES = tc::operand_bytes(PT);
+constexpr uint32_t B_BYTES = tc::operand_bytes(NB);
+// one stage: A hi, A lo, A' hi, A' lo (A' = -i A), B hi, B lo
+constexpr uint32_t STAGE_BYTES = 4 * A_BYTES + 2 * B_BYTES;
+constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES;
+constexpr uint32_t TMEM_COLS = 512;
+static_assert(SMEM_BYTES + 1024 <= 227 * 1024, "shared memory");
+static_assert(STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "operand alignment");
+
+struct SplitParams {
+    int na, ntime, nchan, nsrc, ntiles;
+    long long nbl;
+    int has_gains, has_weight, has_pointing;
+    const int2 *tiles;        // (p0, q0) of each tile
+    const ChanF *chan;
+    const float2 *tau;        // [ntime][nsrc][na] double-float delays (s)
+    const float *rho;         // [ntime][nsrc][na] beam radii
+    const float *scale;       // [scale_trows][nchan][nsrc][4]: X_s (nu/nu_ref)^alpha, times E_s^2 without pointing
+    int scale_trows;          // ntime (time-varying brightness) or 1
+    const float2 *gains;      // [ntime][na][nchan][4]
+    const float2 *data;       // [ntime][nbl][nchan][4]
+    const float *weight;      // [ntime][nbl][nchan]
+    float2 *vis_out;
+    double *partials;
+    unsigned *counter;
+    double *result;
+    DevStatus *status;
+};
+
+// K = exp(2 pi i nu tau) with nu tau reduced exactly to about [-1/2, 1/2]
+// turns in double-float arithmetic, then the SFU sine and cosine.
+__device__ __forceinline__ float2 phase_sfu(float2 tau, const ChanF &ch) {
+    const float p = ch.nu_hi * tau.x;
+    const float e = fmaf(ch.nu_hi, tau.x, -p);
+    const float r = p - round_int_f(p);
+    const float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
+    float sn, cs;
+    __sincosf(6.28318530717958648f * f, &sn, &cs);
+    return make_float2(cs, sn);
+}
+__device__ __forceinline__ float beam_f(float rho, const ChanF &ch) {
+    const float x = ch.cnu * rho;
+    const float cb = cosf(x);
+    return x < 1.57079632679f ? cb * cb * cb : 0.f;
+}
+
+// (x, y) -> packed hi and lo words: BF16 pairs (x in the low half).
+__device__ __forceinline__ uint32_t pack_bf16(float x, float y) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(y), "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_bf16(float x, float y, uint32_t &hi, uint32_t &lo) {
+    hi = pack_bf16(x, y);
+    lo = pack_bf16(x - __uint_as_float(hi << 16), y - __uint_as_float(hi & 0xffff0000u));
+}
+// (x, y) word -> (y, -x): the same pair multiplied by -i
+__device__ __forceinline__ uint32_t rot_bf16(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
+// TF32: round to nearest (ties away) into the 19 bits the tensor core reads.
+__device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void st16(unsigned char *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
+}
+
+// Operands of one pipeline stage. BF16: 8 sources (K = 16); TF32: 4 (K = 8).
+// Element (row, source j, part c) sits at K index 2 j + c.
+template <bool TF32>
+struct Producer {
+    static constexpr int SPS = TF32 ? 4 : 8;
+    // this thread's A item (p, quad h) and B item (q, quad h, Stokes pair xp)
+    bool hasA, hasB;
+    int pA, hA, qB, hB, xp;
+
+    __device__ void init(int tid) {
+        if (TF32) {
+            hasA = tid < 128;
+            hasB = !hasA;
+            pA = tid & 127;
+            hA = 0;
+            qB = tid & 63;
+            hB = 0;
+            xp = (tid >> 6) & 1;
+        } else {
+            hasA = hasB = true;
+            pA = tid & 127;
+            hA = tid >> 7;
+            qB = tid & 63;
+            hB = (tid >> 6) & 1;
+            xp = tid >> 7;
+        }
+    }
+};
+
+template <bool TF32, bool WRITE>
+__global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
+    constexpr int SPS = Producer<TF32>::SPS;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t full[NST], empty[NST], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, sLast;
+    __shared__ double red[THREADS / 32];
+
+    if (inputs_bad(P.status)) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x % P.ntiles;
+    const int rest = blockIdx.x / P.ntiles;
+    const int k = rest % P.nchan;
+    const int t = rest / P.nchan;
+    const int2 pq = P.tiles[tile];
+    const int p0 = pq.x, q0 = pq.y;
+    const ChanF ch = P.chan[k];
+    const int nstg = (P.nsrc + SPS - 1) / SPS;
+
+    if (tid == 0) {
+        for (int i = 0; i < NST; i++) {
+            tc::mbar_init(&full[i], NPROD);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&done, 1);
+        abort_flag = 0;
+        tc::fence_async_smem();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    double chi = 0.0;
+
+    if (warp < NPROD / 32) {
+        // ------------------------------------------------------------ producers
+        Producer<TF32> pr;
+        pr.init(tid);
+        const int pg = p0 + pr.pA, qg = q0 + pr.qB;
+        // per-source scales of this (t, k): X_s (nu/nu_ref)^alpha [E_s^2]
+        const float *scale = P.scale + ((long long)(P.scale_trows > 1 ? t : 0) * P.nchan + k) * 4LL * P.nsrc;
+        const bool pointing = P.has_pointing != 0;
+        // inputs of one stage, loaded a stage ahead of their use
+        struct Pre {
+            float2 ta[4], tb[4], xs[4];
+            float ra[4], rb[4];
+        };
+        auto load = [&](int it, Pre &L) {
+            const int s0 = it * SPS;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int sa = s0 + 4 * pr.hA + j, sb = s0 + 4 * pr.hB + j;
+                L.ta[j] = L.tb[j] = L.xs[j] = make_float2(0.f, 0.f);
+                L.ra[j] = L.rb[j] = 0.f;
+                if (pr.hasA && sa < P.nsrc && pg < P.na) {
+                    const long long di = ((long long)t * P.nsrc + sa) * P.na + pg;
+                    L.ta[j] = P.tau[di];
+                    if (pointing) L.ra[j] = P.rho[di];
+                }
+                if (pr.hasB && sb < P.nsrc && qg < P.na) {
+                    const long long db = ((long long)t * P.nsrc + sb) * P.na + qg;
+                    L.tb[j] = P.tau[db];
+                    if (pointing) L.rb[j] = P.rho[db];
+                    L.xs[j] = *reinterpret_cast<const float2 *>(scale + 4LL * sb + 2 * pr.xp);
+                }
+            }
+        };
+        Pre cur, nxt;
+        if (nstg > 0) load(0, cur);
+        for (int it = 0; it < nstg; it++) {
+            const int slot = it % NST;
+            const int s0 = it * SPS;
+            if (it + 1 < nstg) load(it + 1, nxt);
+            if (!tc::mbar_wait(&empty[slot], ((it / NST) & 1) ^ 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            unsigned char *stg = smem + slot * STAGE_BYTES;
+            if (pr.hasA) {
+                float2 a[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const bool live = s0 + 4 * pr.hA + j < P.nsrc && pg < P.na;
+                    a[j] = live ? phase_sfu(cur.ta[j], ch) : make_float2(0.f, 0.f);
+                    if (pointing) {
+                        const float E = beam_f(cur.ra[j], ch);
+                        a[j].x *= E;
+                        a[j].y *= E;
+                    }
+                }
+                if (TF32) {
+                    uint32_t h[8], l[8];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        split_tf32(a[j].x, h[2 * j], l[2 * j]);
+                        split_tf32(a[j].y, h[2 * j + 1], l[2 * j + 1]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 2; c++) {   // 16-byte halves: sources (0, 1), (2, 3)
+                        const uint32_t o = tc::operand_offset(pr.pA, 16 * c);
+                        const int b = 4 * c;
+                        st16(stg + o, h[b], h[b + 1], h[b + 2], h[b + 3]);
+                        st16(stg + A_BYTES + o, l[b], l[b + 1], l[b + 2], l[b + 3]);
+                        // -i A: (re, im) -> (im, -re)
+                        st16(stg + 2 * A_BYTES + o, h[b + 1], h[b] ^ 0x80000000u, h[b + 3], h[b + 2] ^ 0x80000000u);
+                        st16(stg + 3 * A_BYTES + o, l[b + 1], l[b] ^ 0x80000000u, l[b + 3], l[b + 2] ^ 0x80000000u);
+                    }
+                } else {
+                    uint32_t h[4], l[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
+                    const uint32_t o = tc::operand_offset(pr.pA, 16 * pr.hA);
+                    st16(stg + o, h[0], h[1], h[2], h[3]);
+                    st16(stg + A_BYTES + o, l[0], l[1], l[2], l[3]);
+                    st16(stg + 2 * A_BYTES + o, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
+                    st16(stg + 3 * A_BYTES + o, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
+                }
+            }
+            if (pr.hasB) {
+                float2 b[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const bool live = s0 + 4 * pr.hB + j < P.nsrc && qg < P.na;
+                    b[j] = live ? phase_sfu(cur.tb[j], ch) : make_float2(0.f, 0.f);
+                    if (pointing) {
+                        const float E = beam_f(cur.rb[j], ch);
+                        b[j].x *= E;
+                        b[j].y *= E;
+                    }
+                }
+#pragma unroll
+                for (int x = 0; x < 2; x++) {   // Stokes X = 2 xp + x
+                    const int row = 4 * pr.qB + 2 * pr.xp + x;
+                    if (TF32) {
+                        uint32_t h[8], l[8];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const float X = x ? cur.xs[j].y : cur.xs[j].x;
+                            split_tf32(X * b[j].x, h[2 * j], l[2 * j]);
+                            split_tf32(X * b[j].y, h[2 * j + 1], l[2 * j + 1]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < 2; c++) {
+                            const uint32_t o = tc::operand_offset(row, 16 * c);
+                            st16(stg + 4 * A_BYTES + o, h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+                            st16(stg + 4 * A_BYTES + B_BYTES + o, l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
+                        }
+                    } else {
+                        uint32_t h[4], l[4];
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            const float X = x ? cur.xs[j].y : cur.xs[j].x;
+                            split_bf16(X * b[j].x, X * b[j].y, h[j], l[j]);
+                        }
+                        const uint32_t o = tc::operand_offset(row, 16 * pr.hB);
+                        st16(stg + 4 * A_BYTES + o, h[0], h[1], h[2], h[3]);
+                        st16(stg + 4 * A_BYTES + B_BYTES + o, l[0], l[1], l[2], l[3]);
+                    }
+                }
+            }
+            tc::fence_async_smem();
+            tc::mbar_arrive(&full[slot]);
+            cur = nxt;
+        }
+
+        // ------------------------------------------------------------ epilogue
+        bool ok = abort_flag == 0;
+        if (ok && nstg > 0) ok = tc::mbar_wait(&done, 0, &abort_flag);
+        ok = __all_sync(0xffffffffu, ok);
+        tc::tc_fence_after();
+        if (ok) {
+            const int quad = warp & 3, qh = warp >> 2;
+            const int p = 32 * quad + lane, pgl = p0 + p;
+            const bool prow = pgl < P.na;
+            float2 gp[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
+            if (P.has_gains && prow) {
+                const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + pgl) * P.nchan + k));
+                const float4 a01 = g4[0], a23 = g4[1];
+                gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
+                gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
+            }
+            const uint32_t lane_addr = tmem + ((uint32_t)(32 * quad) << 16);
+            for (int qq = 0; qq < 32; qq += 2) {
+                const int ql = 32 * qh + qq;
+                uint32_t re[8] = {0, 0, 0, 0, 0, 0, 0, 0}, im[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (nstg > 0) {
+                    tc::tmem_ld8(lane_addr + 4 * ql, re);
+                    tc::tmem_ld8(lane_addr + 256 + 4 * ql, im);
+                    tc::tmem_wait_ld(re);
+                    tc::tmem_wait_ld(im);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    const int q = q0 + ql + i;
+                    if (!(prow && pgl < q && q < P.na)) continue;
+                    const float Ir = __uint_as_float(re[4 * i]), Ii = __uint_as_float(im[4 * i]);
+                    const float Qr = __uint_as_float(re[4 * i + 1]), Qi = __uint_as_float(im[4 * i + 1]);
+                    const float Ur = __uint_as_float(re[4 * i + 2]), Ui = __uint_as_float(im[4 * i + 2]);
+                    const float Vr = __uint_as_float(re[4 * i + 3]), Vi = __uint_as_float(im[4 * i + 3]);
+                    float2 Sm[4];
+                    Sm[0] = make_float2(Ir + Qr, Ii + Qi);   // I + Q
+                    Sm[1] = make_float2(Ur - Vi, Ui + Vr);   // U + iV
+                    Sm[2] = make_float2(Ur + Vi, Ui - Vr);   // U - iV
+                    Sm[3] = make_float2(Ir - Qr, Ii - Qi);   // I - Q
+                    float2 gq[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
+                    if (P.has_gains) {
+                        const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
+                        const float4 b01 = g4[0], b23 = g4[1];
+                        gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
+                        gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
+                    }
+                    float2 V[4], tmp[4], gqh[4];
+                    mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
+                    mherm(gq, gqh);
+                    mmul(tmp, gqh, V);
+                    const long long bl = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 + (q - pgl - 1);
+                    const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
+                    if (WRITE) {
+                        float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * row);
+                        o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
+                        o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
+                    } else {
+                        const float4 *d4 = reinterpret_cast<const float4 *>(P.data + 4 * row);
+                        const float4 d01 = d4[0], d23 = d4[1];
+                        const float2 D[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w),
+                                             make_float2(d23.x, d23.y), make_float2(d23.z, d23.w)};
+                        float r2 = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
+                            r2 += dr * dr + di * di;
+                        }
+                        const float w = P.has_weight ? P.weight[row] : 1.f;
+                        chi += (double)(w * r2);
+                    }
+                }
+            }
+        } else {
+            atomicOr(&P.status->err[EC_RUN], EB_TIMEOUT);
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t idesc = tc::instr_desc(TF32 ? tc::kFmtTF32 : tc::kFmtBF16, PT, NB);
+        const uint32_t sbase = tc::smem_u32(smem);
+        for (int it = 0; it < nstg; it++) {
+            const int slot = it % NST;
+            if (!tc::mbar_wait(&full[slot], (it / NST) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
+            tc::tc_fence_after();
+            const uint32_t sb = sbase + slot * STAGE_BYTES;
+            const uint64_t bh = tc::smem_desc(sb + 4 * A_BYTES), bl = tc::smem_desc(sb + 4 * A_BYTES + B_BYTES);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {   // h = 0: Re S (A), h = 1: Im S (-i A)
+                const uint64_t ah = tc::smem_desc(sb + 2 * h * A_BYTES), alo = tc::smem_desc(sb + (2 * h + 1) * A_BYTES);
+                const uint32_t d = tmem + 256 * h;
+                if (TF32) {
+                    tc::mma_tf32(d, ah, bh, idesc, it > 0);
+                    tc::mma_tf32(d, ah, bl, idesc, 1);
+                    tc::mma_tf32(d, alo, bh, idesc, 1);
+                } else {
+                    tc::mma_bf16(d, ah, bh, idesc, it > 0);
+                    tc::mma_bf16(d, ah, bl, idesc, 1);
+                    tc::mma_bf16(d, alo, bh, idesc, 1);
+                }
+            }
+            tc::mma_commit(&empty[slot]);
+        }
+        tc::mma_commit(&done);
+    }
+
+    // ---------------------------------------------------------------- teardown
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, TMEM_COLS);
+    }
+    if (WRITE) return;
+    // chi^2: block sum, one partial per block, the last block sums them in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) chi += __shfl_down_sync(0xffffffffu, chi, o);
+    if (lane == 0) red[warp] = chi;
+    __syncthreads();
+    if (tid == 0) {
+        double b = 0.0;
+        for (int i = 0; i < THREADS / 32; i++) b += red[i];
+        P.partials[blockIdx.x] = b;
+        __threadfence();
+        const unsigned ticket = atomicAdd(P.counter, 1u);
+        sLast = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!sLast) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += THREADS) s += __ldcg(&P.partials[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < THREADS / 32; i++) tot += red[i];
+        if (P.status->err[EC_RUN] == 0) *P.result = tot;
+        *P.counter = 0u;
+    }
+}
+
+// Per-source factors of the B operand for each (t, k): the Stokes vector
+// times the spectral factor (nu/nu_ref)^alpha (eq. 2) and, without pointing
+// errors, times the beam of both antennas E_s^2 (eq. 4; the same for every
+// antenna). out [trows][nchan][nsrc][4].
+__global__ void k_split_scales(int nsrc, int nchan, int trows, int na, const ChanF *chan, const float *stokes,
+                               const float *alpha, const float *rho, int pointing, float4 *out) {
+    const long long n = (long long)trows * nchan * nsrc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i % nsrc);
+        const long long r = i / nsrc;
+        const int k = (int)(r % nchan);
+        const int t = (int)(r / nchan);
+        const ChanF ch = chan[k];
+        float f = exp2f(2.0f * alpha[s] * ch.hlr);
+        if (!pointing) {
+            const float E = beam_f(rho[(long long)s * na], ch);   // timestep 0, any antenna
+            f *= E * E;
+        }
+        const float4 st = reinterpret_cast<const float4 *>(stokes)[(long long)t * nsrc + s];
+        out[i] = make_float4(st.x * f, st.y * f, st.z * f, st.w * f);
+    }
+}
+
+// Split mode takes point sources only: flags any Gaussian source.
+__global__ void k_check_points(int nsrc, const float *gauss, DevStatus *st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsrc && gauss[4 * s + 3] != 0.f) {
+        atomicOr(&st->err[EC_MODE], EB_RANGE);
+        atomicMin(&st->first_bad[EC_MODE], (long long)s);
+    }
+}
+
+}  // namespace split
+
+// Tiles (p0, q0) with at least one pair p < q inside the array.
+std::vector<int2> split_tiles(int na) {
+    std::vector<int2> v;
+    for (int p0 = 0; p0 < na; p0 += split::PT)
+        for (int q0 = 0; q0 < na; q0 += split::QT)
+            if (p0 < std::min(na, q0 + split::QT) - 1) v.push_back(make_int2(p0, q0));
+    return v;
+}
+
+cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result) {
+    using namespace split;
+    cudaError_t e;
+    if (!c->d_stiles) {
+        std::vector<int2> tl = split_tiles(c->dims.na);
+        Alloc alloc{c};
+        e = alloc((void **)&c->d_stiles, tl.size() * sizeof(int2));
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(c->d_stiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        c->nstiles = (int)tl.size();
+    }
+    const long long blocks = (long long)c->dims.ntime * c->dims.nchan * c->nstiles;
+    if (blocks == 0) return cudaSuccess;
+    if (!write && (size_t)blocks > c->spart_cap) {
+        if (c->d_spart) cudaFree(c->d_spart);
+        c->d_spart = nullptr;
+        c->spart_cap = 0;
+        Alloc alloc{c};
+        e = alloc((void **)&c->d_spart, (size_t)blocks * sizeof(double));
+        if (e != cudaSuccess) return e;
+        c->spart_cap = (size_t)blocks;
+    }
+    if (!c->d_scounter) {
+        Alloc alloc{c};
+        e = alloc((void **)&c->d_scounter, sizeof(unsigned));
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(c->d_scounter, 0, sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = reset_status_class(c, EC_MODE);
+    if (e != cudaSuccess) return e;
+    const int trows = c->time_varying ? c->dims.ntime : 1;
+    const size_t nscale = (size_t)trows * c->dims.nchan * c->nsrc;
+    if (nscale > c->sscale_cap) {
+        if (c->d_sscale) cudaFree(c->d_sscale);
+        c->d_sscale = nullptr;
+        c->sscale_cap = 0;
+        Alloc alloc{c};
+        e = alloc((void **)&c->d_sscale, nscale * sizeof(float4));
+        if (e != cudaSuccess) return e;
+        c->sscale_cap = nscale;
+    }
+    if (c->nsrc > 0) {
+        k_check_points<<<(c->nsrc + 255) / 256, 256, 0, c->stream>>>(c->nsrc, (const float *)c->d_gauss, c->d_status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int nb = (int)std::min<size_t>((nscale + 255) / 256, 4096);
+        k_split_scales<<<nb, 256, 0, c->stream>>>(c->nsrc, c->dims.nchan, trows, c->dims.na,
+                                                  reinterpret_cast<const ChanF *>(c->d_chan),
+                                                  reinterpret_cast<const float *>(c->d_stokes),
+                                                  reinterpret_cast<const float *>(c->d_alpha),
+                                                  reinterpret_cast<const float *>(c->d_rho), c->has_pointing,
+                                                  reinterpret_cast<float4 *>(c->d_sscale));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    SplitParams P{};
+    P.na = c->dims.na;
+    P.ntime = c->dims.ntime;
+    P.nchan = c->dims.nchan;
+    P.nsrc = c->nsrc;
+    P.ntiles = c->nstiles;
+    P.nbl = c->nbl;
+    P.has_gains = c->has_gains;
+    P.has_weight = c->has_weight;
+    P.has_pointing = c->has_pointing;
+    P.tiles = c->d_stiles;
+    P.chan = reinterpret_cast<const ChanF *>(c->d_chan);
+    P.tau = reinterpret_cast<const float2 *>(c->d_tau);
+    P.rho = reinterpret_cast<const float *>(c->d_rho);
+    P.scale = reinterpret_cast<const float *>(c->d_sscale);
+    P.scale_trows = trows;
+    P.gains = reinterpret_cast<const float2 *>(c->d_gains);
+    P.data = reinterpret_cast<const float2 *>(c->d_data);
+    P.weight = reinterpret_cast<const float *>(c->d_weight);
+    P.vis_out = reinterpret_cast<float2 *>(vis_out);
+    P.partials = c->d_spart;
+    P.counter = c->d_scounter;
+    P.result = result;
+    P.status = c->d_status;
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e2 = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e2 != cudaSuccess) return e2;
+        kernel<<<(unsigned)blocks, THREADS, SMEM_BYTES, c->stream>>>(P);
+        return cudaGetLastError();
+    };
+    const bool tf32 = c->tc_mode == RIME_TC_SPLIT_TF32;
+    if (tf32) return write ? go(k_split<true, true>) : go(k_split<true, false>);
+    return write ? go(k_split<false, true>) : go(k_split<false, false>);
+}
+
+}  // namespace rime

@@ -75,6 +75,9 @@ def test_null_context_calls_are_rejected(L):
     assert L.rime_predict(None, None) == 1
     assert L.rime_chi2(None, None) == 1
     assert L.rime_sync(None) == 1
+    assert L.rime_chi2_batched(None, 0, None, None, None) == 1
+    assert L.rime_batched_config(None, None) == 1
+    assert L.rime_set_batched_config(None, None) == 1
     L.rime_destroy(None)   # ignored
 
 

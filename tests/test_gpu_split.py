@@ -1,0 +1,148 @@
+"""The split-precision tensor-core form of the point-source sum
+(rime_set_tensor_mode): visibilities and chi^2 against the FP64 oracle at the
+error each split states, its degenerate and error cases, and sampled
+visibilities at the 256-antenna, 4096-source size."""
+import numpy as np
+import pytest
+
+import oracle
+import rime_synth
+from gpu_cases import gpu_ctx, make_case, rel_err, vis_err
+
+pytestmark = pytest.mark.gpu
+
+# Error bounds against the FP64 oracle. Visibilities: max |dV| / max |V|.
+# A product of split operands keeps hi*hi + hi*lo + lo*hi; what is lost is
+# the rounding of the low parts (relative 2^-17 for BF16 pairs, 2^-22 for TF32
+# pairs) and the SFU sine/cosine (absolute ~2^-21), accumulated over the
+# sources with random signs. The tensor core's FP32 accumulator also drops
+# about one unit in the last place of the running sum per MMA (measured), a
+# bias that grows with the number of MMAs into one accumulator: 1536 (BF16)
+# and 3072 (TF32) for 4096 sources. chi^2 inherits |dV|^2 / |V - D|^2 with
+# V - D at the 0.01 Jy noise level.
+VTOL = {"bf16": 1e-4, "tf32": 1e-4}
+CTOL = {"bf16": 2e-2, "tf32": 1e-4}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _mode(name):
+    import paper_1501_07719_gb300 as R
+    return {"bf16": R.RIME_TC_SPLIT_BF16, "tf32": R.RIME_TC_SPLIT_TF32}[name]
+
+
+CASES = {
+    # one tile pair, ragged source count (37 = 4 chunks of 8 + 5)
+    "13ant-37src": dict(wl=rime_synth.custom(13, 2, 3, 37, 0, seed_index=71)),
+    # two row tiles and three column tiles with ragged edges, pointing errors
+    "130ant-pointing": dict(wl=rime_synth.custom(130, 1, 2, 20, 0, seed_index=72), pointing_sigma=0.004),
+    # no gains, unit weights, a single channel and source
+    "9ant-1src": dict(wl=rime_synth.custom(9, 2, 1, 1, 0, seed_index=73), gains=False, unit_weights=True),
+    # time-varying brightness
+    "20ant-tv": dict(wl=rime_synth.custom(20, 3, 2, 12, 0, seed_index=74), time_varying=True),
+}
+
+
+@pytest.mark.parametrize("split", ["bf16", "tf32"])
+@pytest.mark.parametrize("case", list(CASES))
+def test_split_matches_oracle(case, split):
+    inp = make_case(precision="f32", **CASES[case])
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(_mode(split))
+    V = r.predict().cpu().numpy()
+    chi = r.chi2()
+    r.close()
+    ev = vis_err(V, inp["oracle_vis"])
+    ec = rel_err(chi, oracle.Problem(inp, data=inp["data"]).chi2())
+    assert ev <= VTOL[split], ev
+    assert ec <= CTOL[split], ec
+
+
+def test_split_mode_switch_restores_the_direct_path():
+    import paper_1501_07719_gb300 as R
+    inp = make_case(rime_synth.custom(13, 2, 3, 9, 0, seed_index=75), "f32")
+    r = gpu_ctx(inp, "f32")
+    direct = r.chi2()
+    r.set_tensor_mode(R.RIME_TC_SPLIT_TF32)
+    split = r.chi2()
+    r.set_tensor_mode(R.RIME_TC_OFF)
+    again = r.chi2()
+    r.close()
+    assert again == direct and split != direct
+
+
+def test_split_is_deterministic():
+    inp = make_case(rime_synth.custom(70, 2, 2, 30, 0, seed_index=76), "f32")
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(_mode("bf16"))
+    a, b = r.chi2(), r.chi2()
+    r.close()
+    assert a == b
+
+
+def test_split_without_sources_gives_zero_model():
+    inp = make_case(rime_synth.custom(10, 2, 2, 0, 0, seed_index=77), "f32")
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(_mode("tf32"))
+    V = r.predict().cpu().numpy()
+    chi = r.chi2()
+    r.close()
+    assert np.all(V == 0)
+    want = oracle.Problem(inp, data=inp["data"]).chi2()
+    assert rel_err(chi, want) <= 1e-6
+
+
+def test_split_rejects_gaussian_sources_and_fp64():
+    import paper_1501_07719_gb300 as R
+    inp = make_case(rime_synth.custom(8, 2, 2, 3, 2, seed_index=78), "f32")
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(R.RIME_TC_SPLIT_BF16)
+    out = r.torch.full((2, 28, 2, 4), 3.0 + 1j, dtype=r.cdtype, device="cuda")
+    r.predict(out)
+    with pytest.raises(R.RimeError) as e:
+        r.sync()
+    assert e.value.status == R._abi.RIME_E_INVALID and "point sources" in str(e.value)
+    assert bool((out == 3.0 + 1j).all())
+    r.set_tensor_mode(R.RIME_TC_OFF)       # the direct path takes the same model
+    assert rel_err(r.chi2(), oracle.Problem(inp, data=inp["data"]).chi2()) <= 1e-4
+    r.close()
+    inp64 = make_case(rime_synth.custom(5, 1, 1, 1, 0, seed_index=79), "f64")
+    r = gpu_ctx(inp64, "f64")
+    with pytest.raises(R.RimeError):
+        r.set_tensor_mode(R.RIME_TC_SPLIT_TF32)
+    with pytest.raises(R.RimeError):
+        r.set_tensor_mode(7)
+    r.close()
+
+
+@pytest.mark.parametrize("split", ["bf16", "tf32"])
+def test_split_full_256ant_sampled(split):
+    """The 256-antenna, 20-timestep, 128-channel, 4096-point workload in the
+    benchmark's configuration: sampled visibilities against the oracle."""
+    import torch
+    import paper_1501_07719_gb300 as R
+    inp = rime_synth.make_inputs("256ant-20t-128ch-4096pt", precision="f32")
+    r = R.Rime(inp, R.RIME_FP32, weight=inp["weight"].astype(np.float32))
+    r.set_gains(inp["gains"])
+    r.set_sources(inp["sources"])
+    r.set_tensor_mode(_mode(split))
+    V = r.predict()
+    r.close()
+    rng = np.random.default_rng(1)
+    n = 192
+    t = rng.integers(0, 20, n)
+    bl = rng.integers(0, 32640, n)
+    k = rng.integers(0, 128, n)
+    tb, blb, kb = (torch.tensor(a, device="cuda") for a in (t, bl, k))
+    got = V[tb, blb, kb].cpu().numpy().astype(np.complex128)
+    del V
+    torch.cuda.empty_cache()
+    p, q = rime_synth.baseline_pairs(256)
+    ref = oracle.Problem(inp).vis_list(t, p[bl], q[bl], k)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err <= VTOL[split], err
