@@ -126,6 +126,168 @@ def cpu_baseline(wl, inp, nt=None, nch=None):
                       f"({terms / 4:.3g} source-terms), FP64, {dt:.1f} s"}
 
 
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+
+
+def _timed(torch, stream, fn, reps):
+    """Median device time (ms) of fn() over reps calls, events on the stream."""
+    ev = _events(torch, reps)
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def form_grad(torch, R, chi2_ms):
+    """Adjoint gradient (rime_chi2_grad) on the 64-antenna gradient workload,
+    against the plain fused chi^2 of the same workload."""
+    wl = rime_synth.WORKLOADS["64ant-100t-64ch-100pt100g-grad"]
+    inp = rime_synth.make_inputs(wl, precision="f32")
+    w = inp["weight"].astype(np.float32)
+    ctx = R.Rime(inp, R.RIME_FP32, weight=w)
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])
+    V = ctx.predict()
+    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64), w)
+    del V
+    stream = torch.cuda.current_stream()
+    gs = torch.zeros((wl.nsrc, 10), dtype=torch.float64, device="cuda")
+    gg = torch.zeros((wl.ntime, wl.na, wl.nchan, 2, 2), dtype=torch.complex128, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        R.rime_chi2_grad(ctx.ctx, gs, gg)
+    grad_ms = _timed(torch, stream, lambda: R.rime_chi2_grad(ctx.ctx, gs, gg), 5)
+    plain_ms = _timed(torch, stream, lambda: ctx.chi2_async(out), 20)
+    ctx.close()
+    nparam = 10 * wl.nsrc
+    return {"workload": wl.name, "dtype": "f32", "chi2_grad_ms": grad_ms, "chi2_ms": plain_ms,
+            "grad_over_chi2": grad_ms / plain_ms,
+            "speedup_vs_central_fd_of_source_params": 2 * nparam * plain_ms / grad_ms,
+            "fd_basis": f"central differences need 2 x {nparam} chi^2 evaluations for the source "
+                        "parameters alone; the adjoint also returns the gains gradient",
+            "outputs": "chi^2, d/d(l, m, I, Q, U, V, alpha, major, minor, pa) per source, d/dG per "
+                       "(t, antenna, channel, Jones entry)"}
+
+
+def form_batched(torch, R):
+    """Batched chi^2 of 512 sky models (5..500 sources each) against one shared
+    observation: one persistent launch replayed from a CUDA graph, against 512
+    plain rime_chi2_async calls (one per set) on the same GPU."""
+    wl = rime_synth.WORKLOADS["64ant-50t-32ch-512sets"]
+    inp = rime_synth.make_inputs(wl, precision="f32")
+    sets = inp["sets"]
+    off = sets["offsets"]
+    nsets = len(off) - 1
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = inp["weight"].astype(np.float32)
+    ctx = R.Rime(inp, R.RIME_FP32, weight=w, stream=stream)
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])          # the 100-source truth sky
+    V = ctx.predict()
+    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64), w)
+    del V
+    dev = {k: torch.tensor(np.ascontiguousarray(v), dtype=torch.float64, device="cuda")
+           for k, v in sets["sources"].items()}
+    out = torch.zeros(nsets, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    ctx.chi2_batched(off, dev, out=out)      # buffers + tuning trials
+    ctx.sync()
+    first_s = time.perf_counter() - t0
+    cfg = ctx.batched_config()
+    g = torch.cuda.CUDAGraph()
+    g.capture_begin(capture_error_mode="relaxed")
+    ctx.chi2_batched(off, dev, out=out)
+    g.capture_end()
+    g.replay()
+    torch.cuda.synchronize()
+    batched_ms = _timed(torch, stream, g.replay, 3)
+    ref = out.cpu().numpy().copy()
+    outp = torch.zeros(nsets, dtype=torch.float64, device="cuda")
+    views = [{k: v[off[j]:off[j + 1]] for k, v in dev.items()} for j in range(nsets)]
+
+    def plain():
+        for j in range(nsets):
+            ctx.set_sources(views[j])
+            ctx.chi2_async(outp[j:j + 1])
+    plain()
+    plain_ms = _timed(torch, stream, plain, 2)
+    rel = np.abs(outp.cpu().numpy() - ref) / ref
+    ctx.close()
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    isg = sets["sources"]["shape"][:, 0] > 0
+    flops = (FLOPS_POINT * int((~isg).sum()) + FLOPS_GAUSS * int(isg.sum())) * wl.ntime * wl.nbl * wl.nchan
+    return {"workload": wl.name, "dtype": "f32 visibilities, f64 chi^2", "nsets": nsets,
+            "set_nsrc": [int(np.diff(off).min()), int(np.diff(off).max())], "total_sources": int(off[-1]),
+            "batched_ms": batched_ms, "plain_512_calls_ms": plain_ms, "speedup_vs_plain": plain_ms / batched_ms,
+            "chi2_evals_per_s": nsets / (batched_ms * 1e-3),
+            "tflops": flops / (batched_ms * 1e-3) / 1e12, "first_call_s_incl_tuning": first_s,
+            "max_rel_diff_vs_plain": float(rel.max()),
+            "launch": "captured CUDA graph: schedule upload, source prep, one persistent kernel, per-set sums",
+            "tuned": {k: cfg[k] for k in ("channels_per_item", "blocks_per_sm", "order", "tuned")},
+            "trials_ms": [round(t["ms"], 3) for t in cfg["trials"]]}
+
+
+def form_split(torch, R):
+    """Point-source sum as split-precision tcgen05 MMAs (BF16 and TF32 hi+lo)
+    on the 256-antenna, 4096-point workload, against the plain FP32 direct
+    sum; errors against the FP64 oracle on sampled visibilities and, for
+    chi^2, on a one-timestep, two-channel slice of the same workload."""
+    import oracle
+    wl = rime_synth.WORKLOADS["256ant-20t-128ch-4096pt"]
+    inp = rime_synth.make_inputs(wl, precision="f32")
+    w = inp["weight"].astype(np.float32)
+    ctx = R.Rime(inp, R.RIME_FP32, weight=w)
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])
+    V = ctx.predict()
+    D = (V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64)
+    del V
+    ctx.set_data(D, w)
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(3)
+    n = 64
+    t, bl, k = rng.integers(0, wl.ntime, n), rng.integers(0, wl.nbl, n), rng.integers(0, wl.nchan, n)
+    p, q = rime_synth.baseline_pairs(wl.na)
+    vref = oracle.Problem(inp).vis_list(t, p[bl], q[bl], k)
+    # the chi^2 slice: timestep 0, channels 0-1
+    sl = dict(inp, ntime=1, nchan=2, freq=inp["freq"][:2], uvw=inp["uvw"][:1],
+              gains=inp["gains"][:1, :, :2], weight=w[:1, :, :2])
+    Dsl = np.ascontiguousarray(D[:1, :, :2])
+    chi_ref = oracle.Problem(sl, data=Dsl).chi2()
+    csl = R.Rime(sl, R.RIME_FP32, data=Dsl, weight=np.ascontiguousarray(w[:1, :, :2]))
+    csl.set_gains(np.ascontiguousarray(inp["gains"][:1, :, :2]))
+    csl.set_sources(inp["sources"])
+    res = {}
+    for mode, name in ((R.RIME_TC_OFF, "direct_fp32"), (R.RIME_TC_SPLIT_BF16, "split_bf16"),
+                       (R.RIME_TC_SPLIT_TF32, "split_tf32")):
+        ctx.set_tensor_mode(mode)
+        ctx.chi2_async(out)
+        ms = _timed(torch, stream, lambda: ctx.chi2_async(out), 2 if mode == R.RIME_TC_OFF else 5)
+        V = ctx.predict()
+        idx = [torch.tensor(a, device="cuda") for a in (t, bl, k)]
+        got = V[idx[0], idx[1], idx[2]].cpu().numpy().astype(np.complex128)
+        del V
+        torch.cuda.empty_cache()
+        csl.set_tensor_mode(mode)
+        chi_sl = csl.chi2()
+        res[name] = {"ms": ms, "vis_err_vs_fp64": float(np.abs(got - vref).max() / np.abs(vref).max()),
+                     "chi2_rel_err_vs_fp64": abs(chi_sl - chi_ref) / chi_ref}
+    ctx.close()
+    csl.close()
+    for name in ("split_bf16", "split_tf32"):
+        res[name]["speedup_vs_direct"] = res["direct_fp32"]["ms"] / res[name]["ms"]
+    res["workload"] = wl.name
+    res["terms_per_s"] = {kk: terms_of(wl) / (v["ms"] * 1e-3) for kk, v in res.items() if isinstance(v, dict)}
+    res["errors"] = ("vis: max |V - V_fp64| / max |V_fp64| over 64 sampled (t, baseline, channel); "
+                     "chi2: |chi2 - chi2_fp64| / chi2_fp64 on timestep 0, channels 0-1, data = model + noise")
+    return res
+
+
 def run_reference(args, wl, rank, world):
     """The oracle (a deliberately plain FP64 CPU program) on this host's cores:
     each step a bounded sample of the workload, so the run ends within minutes."""
@@ -162,6 +324,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the gradient, batched and split-precision comparisons")
     args = ap.parse_args()
     wl = rime_synth.WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
@@ -283,9 +447,13 @@ def main():
     }
     if clocks:
         line["roofline"]["frac_at_median_clock"] = achieved / peak_fp32_tflops(clocks["sm_mhz"])
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_forms and args.precision == "f32":
+        line["forms"] = {"gradient": form_grad(torch, R, ms_per_step),
+                         "batched": form_batched(torch, R),
+                         "split_precision": form_split(torch, R)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, inp)
-    ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

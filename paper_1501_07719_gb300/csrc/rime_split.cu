@@ -12,7 +12,7 @@
 // the contraction index (K = 2 nsrc) it is two real products,
 //
 //   Re S_X[p, q] = sum_s [Re A_ps, Im A_ps] . X_s [Re A_qs, Im A_qs]
-//   Im S_X[p, q] = sum_s [Im A_ps, -Re A_ps] . X_s [Re A_qs, Im A_qs],
+//   Im S_X[p, q] = sum_s [Re A_ps, Im A_ps] . X_s [-Im A_qs, Re A_qs],
 //
 // which the tensor cores evaluate in FP32 from operands split into a high
 // and a low part (x = hi + lo, hi = x rounded to BF16 or TF32, lo = the
@@ -21,15 +21,23 @@
 // is dropped.
 //
 // One CTA owns (t, k) and a tile of 128 row antennas p (the MMA's M, one
-// TMEM lane each) by 64 column antennas q; the B operand has one row per
-// (q, X), N = 256, and the two accumulators (Re and Im parts, 256 FP32
-// columns each) fill the SM's 512 TMEM columns. Eight producer warps form
-// the operands of each chunk of sources straight into shared memory: the
-// phase nu tau is reduced exactly in double-float arithmetic (the delays
-// tau come from the FP64 upload kernel) and its sine and cosine are taken
-// with the SFU; one thread issues the MMAs; a six-stage mbarrier pipeline
-// connects them. The epilogue reads the accumulators from TMEM, applies the
-// Stokes combination (eq. 2) and the gains (eq. 1), and writes V or forms
+// TMEM lane each) by 32 column antennas q; the B operand has one row per
+// (q, X) for the real parts and one per (q, X) for the imaginary parts,
+// N = 256, so one MMA reads A once for both. Twelve producer warps form the
+// operands of each chunk of
+// sources straight into shared memory: the phase nu tau is reduced exactly in
+// double-float arithmetic (the delays tau come from the FP64 upload kernel)
+// and its sine and cosine are taken with the SFU; one thread issues the
+// MMAs; a three-stage mbarrier pipeline connects them.
+//
+// The tensor core adds each MMA's products into its FP32 accumulator with
+// truncation, losing about one unit in the last place of the running sum per
+// MMA, a bias toward zero that grows with the number of MMAs into one
+// accumulator. So the accumulators (Re and Im, 128 columns each) live in two
+// TMEM buffers used in turn for segments of eight stages: while the MMAs fill
+// one, the producer warps add the other into FP32 running sums in shared
+// memory (round to nearest). The epilogue applies the Stokes combination
+// (eq. 2) and the gains (eq. 1) to the running sums and writes V or forms
 // w |V - D|^2 (eq. 7), summed in FP64.
 #include "rime_internal.cuh"
 #include "rime_dev.cuh"
@@ -42,17 +50,20 @@ namespace rime {
 namespace split {
 
 constexpr int PT = 128;                 // row antennas per tile (MMA M)
-constexpr int QT = 64;                  // column antennas per tile
-constexpr int NB = 4 * QT;              // B rows: (q, X), MMA N
-constexpr int NPROD = 256;              // producer / epilogue threads
+constexpr int QT = 32;                  // column antennas per tile
+constexpr int NB = 8 * QT;              // B rows: (q, X) for Re S, then i (q, X) for Im S; MMA N
+constexpr int NDRAIN = 256;             // A producers, which also drain and run the epilogue
+constexpr int NPROD = NDRAIN + 128;     // and four warps of B producers
 constexpr int THREADS = NPROD + 32;     // and one MMA warp
-constexpr int NST = 6;                  // pipeline stages
+constexpr int NST = 3;                  // pipeline stages
+constexpr int SEG = 8;                  // stages accumulated in TMEM before a drain
 constexpr uint32_t A_BYTES = tc::operand_bytes(PT);
 constexpr uint32_t B_BYTES = tc::operand_bytes(NB);
-// one stage: A hi, A lo, A' hi, A' lo (A' = -i A), B hi, B lo
-constexpr uint32_t STAGE_BYTES = 4 * A_BYTES + 2 * B_BYTES;
-constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES;
-constexpr uint32_t TMEM_COLS = 512;
+// one stage: A hi, A lo, B hi, B lo
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+// + FP32 running sums of the accumulators: 256 columns x 128 rows
+constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES + 256 * 128 * 4;
+constexpr uint32_t TMEM_COLS = 512;     // two buffers of (Re, Im) x 128 columns
 static_assert(SMEM_BYTES + 1024 <= 227 * 1024, "shared memory");
 static_assert(STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "operand alignment");
 
@@ -66,6 +77,7 @@ struct SplitParams {
     const float *rho;         // [ntime][nsrc][na] beam radii
     const float *scale;       // [scale_trows][nchan][nsrc][4]: X_s (nu/nu_ref)^alpha, times E_s^2 without pointing
     int scale_trows;          // ntime (time-varying brightness) or 1
+    int nsrc_pad;             // sources per scale row: nsrc rounded up to a whole stage, zero past nsrc
     const float2 *gains;      // [ntime][na][nchan][4]
     const float2 *data;       // [ntime][nbl][nchan][4]
     const float *weight;      // [ntime][nbl][nchan]
@@ -103,8 +115,8 @@ __device__ __forceinline__ void split_bf16(float x, float y, uint32_t &hi, uint3
     hi = pack_bf16(x, y);
     lo = pack_bf16(x - __uint_as_float(hi << 16), y - __uint_as_float(hi & 0xffff0000u));
 }
-// (x, y) word -> (y, -x): the same pair multiplied by -i
-__device__ __forceinline__ uint32_t rot_bf16(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
+// (x, y) word -> (-y, x): the same pair multiplied by i
+__device__ __forceinline__ uint32_t rot_bf16(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x00008000u; }
 // TF32: round to nearest (ties away) into the 19 bits the tensor core reads.
 __device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
@@ -116,40 +128,25 @@ __device__ __forceinline__ void st16(unsigned char *p, uint32_t a, uint32_t b, u
     *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
 }
 
-// Operands of one pipeline stage. BF16: 8 sources (K = 16); TF32: 4 (K = 8).
-// Element (row, source j, part c) sits at K index 2 j + c.
+// Operands of one pipeline stage: BF16 8 sources (K = 16), TF32 4 (K = 8),
+// as two 16-byte chunks per operand row. Element (row, source j, part c)
+// sits at K index 2 j + c. Warps 0-7 form A (thread: row p, chunk), drain
+// the accumulators and run the epilogue; warps 8-11 form B (thread: antenna
+// q, chunk and a pair of Stokes parameters: rows (q, X) and i (q, X) from one
+// phase); warp 12 issues the MMAs. Sources past the end read the last source's delays and
+// meet a zero Stokes scale, so they add nothing; rows and columns past the
+// last antenna are never read back.
 template <bool TF32>
-struct Producer {
-    static constexpr int SPS = TF32 ? 4 : 8;
-    // this thread's A item (p, quad h) and B item (q, quad h, Stokes pair xp)
-    bool hasA, hasB;
-    int pA, hA, qB, hB, xp;
-
-    __device__ void init(int tid) {
-        if (TF32) {
-            hasA = tid < 128;
-            hasB = !hasA;
-            pA = tid & 127;
-            hA = 0;
-            qB = tid & 63;
-            hB = 0;
-            xp = (tid >> 6) & 1;
-        } else {
-            hasA = hasB = true;
-            pA = tid & 127;
-            hA = tid >> 7;
-            qB = tid & 63;
-            hB = (tid >> 6) & 1;
-            xp = tid >> 7;
-        }
-    }
+struct Item {
+    static constexpr int SPC = TF32 ? 2 : 4;   // sources per chunk
+    static constexpr int SPS = 2 * SPC;        // sources per stage
 };
 
 template <bool TF32, bool WRITE>
 __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
-    constexpr int SPS = Producer<TF32>::SPS;
+    constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[NST], empty[NST], done;
+    __shared__ uint64_t full[NST], empty[NST], seg_full[2], seg_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, sLast;
     __shared__ double red[THREADS / 32];
@@ -164,13 +161,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     const int p0 = pq.x, q0 = pq.y;
     const ChanF ch = P.chan[k];
     const int nstg = (P.nsrc + SPS - 1) / SPS;
+    const int nseg = (nstg + SEG - 1) / SEG;
+    float *totals = reinterpret_cast<float *>(smem + NST * STAGE_BYTES);   // [256 columns][128 rows]
 
     if (tid == 0) {
         for (int i = 0; i < NST; i++) {
             tc::mbar_init(&full[i], NPROD);
             tc::mbar_init(&empty[i], 1);
         }
-        tc::mbar_init(&done, 1);
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(&seg_full[i], 1);
+            tc::mbar_init(&seg_empty[i], NDRAIN);
+        }
         abort_flag = 0;
         tc::fence_async_smem();
     }
@@ -183,218 +185,242 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     double chi = 0.0;
+    const bool pointing = P.has_pointing != 0;
 
     if (warp < NPROD / 32) {
         // ------------------------------------------------------------ producers
-        Producer<TF32> pr;
-        pr.init(tid);
-        const int pg = p0 + pr.pA, qg = q0 + pr.qB;
-        // per-source scales of this (t, k): X_s (nu/nu_ref)^alpha [E_s^2]
-        const float *scale = P.scale + ((long long)(P.scale_trows > 1 ? t : 0) * P.nchan + k) * 4LL * P.nsrc;
-        const bool pointing = P.has_pointing != 0;
-        // inputs of one stage, loaded a stage ahead of their use
+        const bool isA = warp < NDRAIN / 32;
+        const int bw = warp - NDRAIN / 32;                    // B warp: chunk and Stokes pair
+        const int row = isA ? (tid & 127) : lane;             // tile-local p (A) or q (B)
+        const int chunk = isA ? (tid >> 7) : (bw & 1);
+        const int xp = bw >> 1;                               // B: Stokes X = 2 xp, 2 xp + 1
+        const int ant = min((isA ? p0 : q0) + row, P.na - 1);
+        const long long tbase = (long long)t * P.nsrc * P.na + ant;
+        const float4 *scale = reinterpret_cast<const float4 *>(P.scale) +
+                              (long long)(P.scale_trows > 1 ? t : 0) * P.nchan * P.nsrc_pad + (long long)k * P.nsrc_pad;
+        const uint32_t o_row = tc::operand_offset(isA ? row : 4 * row + 2 * xp, 16 * chunk);
+        const uint32_t o_im = tc::operand_offset(4 * QT + 4 * row + 2 * xp, 16 * chunk);   // B rows of Im S
+        // drain / epilogue geometry (A warps): TMEM lanes of this warp and the
+        // 64 + 64 accumulator columns this thread owns
+        const int quad = warp & 3, half = (warp >> 2) & 1;
+        const int lrow = 32 * quad + lane;
+
         struct Pre {
-            float2 ta[4], tb[4], xs[4];
-            float ra[4], rb[4];
+            float2 tau[SPC];
+            float rho[SPC];
+            float4 x[SPC];
         };
         auto load = [&](int it, Pre &L) {
-            const int s0 = it * SPS;
+            const int sb = it * SPS + chunk * SPC;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int sa = s0 + 4 * pr.hA + j, sb = s0 + 4 * pr.hB + j;
-                L.ta[j] = L.tb[j] = L.xs[j] = make_float2(0.f, 0.f);
-                L.ra[j] = L.rb[j] = 0.f;
-                if (pr.hasA && sa < P.nsrc && pg < P.na) {
-                    const long long di = ((long long)t * P.nsrc + sa) * P.na + pg;
-                    L.ta[j] = P.tau[di];
-                    if (pointing) L.ra[j] = P.rho[di];
-                }
-                if (pr.hasB && sb < P.nsrc && qg < P.na) {
-                    const long long db = ((long long)t * P.nsrc + sb) * P.na + qg;
-                    L.tb[j] = P.tau[db];
-                    if (pointing) L.rb[j] = P.rho[db];
-                    L.xs[j] = *reinterpret_cast<const float2 *>(scale + 4LL * sb + 2 * pr.xp);
-                }
+            for (int j = 0; j < SPC; j++) {
+                const int s = min(sb + j, P.nsrc - 1);
+                const long long o = tbase + (long long)s * P.na;
+                L.tau[j] = P.tau[o];
+                L.rho[j] = pointing ? P.rho[o] : 0.f;
+                if (!isA) L.x[j] = scale[sb + j];
             }
         };
-        Pre cur, nxt;
-        if (nstg > 0) load(0, cur);
-        for (int it = 0; it < nstg; it++) {
-            const int slot = it % NST;
-            const int s0 = it * SPS;
-            if (it + 1 < nstg) load(it + 1, nxt);
-            if (!tc::mbar_wait(&empty[slot], ((it / NST) & 1) ^ 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            unsigned char *stg = smem + slot * STAGE_BYTES;
-            if (pr.hasA) {
-                float2 a[4];
+        int nd = 0;   // next segment to drain
+        auto drain = [&]() {
+            const int b = nd & 1;
+            tc::tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const bool live = s0 + 4 * pr.hA + j < P.nsrc && pg < P.na;
-                    a[j] = live ? phase_sfu(cur.ta[j], ch) : make_float2(0.f, 0.f);
-                    if (pointing) {
-                        const float E = beam_f(cur.ra[j], ch);
-                        a[j].x *= E;
-                        a[j].y *= E;
+            for (int h = 0; h < 2; h++)   // Re, Im
+#pragma unroll
+                for (int c2 = 0; c2 < 2; c2++) {
+                    uint32_t r[32];
+                    const int col0 = 128 * h + 64 * half + 32 * c2;
+                    tc::tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + 256 * b + col0, r);
+                    tc::tmem_wait_ld32(r);
+                    float *tot = totals + col0 * 128 + lrow;
+                    if (nd == 0) {
+#pragma unroll
+                        for (int c = 0; c < 32; c++) tot[c * 128] = __uint_as_float(r[c]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; c++) tot[c * 128] += __uint_as_float(r[c]);
                     }
                 }
-                if (TF32) {
-                    uint32_t h[8], l[8];
+            tc::tc_fence_before();
+            tc::mbar_arrive(&seg_empty[b]);
+            nd++;
+        };
+        // warp-uniform: is the next segment complete?
+        auto ready = [&]() -> bool {
+            bool r = false;
+            if (lane == 0) r = nd < nseg && tc::mbar_try_wait(&seg_full[nd & 1], (nd >> 1) & 1);
+            return __shfl_sync(0xffffffffu, r, 0);
+        };
+        auto produce = [&](int it, const Pre &L) {
+            unsigned char *stg = smem + (it % NST) * STAGE_BYTES;
+            float2 a[SPC];
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
+            for (int j = 0; j < SPC; j++) {
+                a[j] = phase_sfu(L.tau[j], ch);
+                if (pointing) {
+                    const float E = beam_f(L.rho[j], ch);
+                    a[j].x *= E;
+                    a[j].y *= E;
+                }
+            }
+            if (isA) {
+                uint32_t h[4], l[4];
+                if (TF32) {
+#pragma unroll
+                    for (int j = 0; j < SPC; j++) {
                         split_tf32(a[j].x, h[2 * j], l[2 * j]);
                         split_tf32(a[j].y, h[2 * j + 1], l[2 * j + 1]);
                     }
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {   // 16-byte halves: sources (0, 1), (2, 3)
-                        const uint32_t o = tc::operand_offset(pr.pA, 16 * c);
-                        const int b = 4 * c;
-                        st16(stg + o, h[b], h[b + 1], h[b + 2], h[b + 3]);
-                        st16(stg + A_BYTES + o, l[b], l[b + 1], l[b + 2], l[b + 3]);
-                        // -i A: (re, im) -> (im, -re)
-                        st16(stg + 2 * A_BYTES + o, h[b + 1], h[b] ^ 0x80000000u, h[b + 3], h[b + 2] ^ 0x80000000u);
-                        st16(stg + 3 * A_BYTES + o, l[b + 1], l[b] ^ 0x80000000u, l[b + 3], l[b + 2] ^ 0x80000000u);
-                    }
                 } else {
+#pragma unroll
+                    for (int j = 0; j < SPC; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
+                }
+                st16(stg + o_row, h[0], h[1], h[2], h[3]);
+                st16(stg + A_BYTES + o_row, l[0], l[1], l[2], l[3]);
+            } else {
+#pragma unroll
+                for (int x = 0; x < 2; x++) {   // B rows (q, X): X_s A_qs, and i X_s A_qs
                     uint32_t h[4], l[4];
 #pragma unroll
-                    for (int j = 0; j < 4; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
-                    const uint32_t o = tc::operand_offset(pr.pA, 16 * pr.hA);
-                    st16(stg + o, h[0], h[1], h[2], h[3]);
-                    st16(stg + A_BYTES + o, l[0], l[1], l[2], l[3]);
-                    st16(stg + 2 * A_BYTES + o, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
-                    st16(stg + 3 * A_BYTES + o, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
-                }
-            }
-            if (pr.hasB) {
-                float2 b[4];
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const bool live = s0 + 4 * pr.hB + j < P.nsrc && qg < P.na;
-                    b[j] = live ? phase_sfu(cur.tb[j], ch) : make_float2(0.f, 0.f);
-                    if (pointing) {
-                        const float E = beam_f(cur.rb[j], ch);
-                        b[j].x *= E;
-                        b[j].y *= E;
+                    for (int j = 0; j < SPC; j++) {
+                        const float X = xp == 0 ? (x == 0 ? L.x[j].x : L.x[j].y) : (x == 0 ? L.x[j].z : L.x[j].w);
+                        if (TF32) {
+                            split_tf32(X * a[j].x, h[2 * j], l[2 * j]);
+                            split_tf32(X * a[j].y, h[2 * j + 1], l[2 * j + 1]);
+                        } else {
+                            split_bf16(X * a[j].x, X * a[j].y, h[j], l[j]);
+                        }
                     }
-                }
-#pragma unroll
-                for (int x = 0; x < 2; x++) {   // Stokes X = 2 xp + x
-                    const int row = 4 * pr.qB + 2 * pr.xp + x;
-                    if (TF32) {
-                        uint32_t h[8], l[8];
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            const float X = x ? cur.xs[j].y : cur.xs[j].x;
-                            split_tf32(X * b[j].x, h[2 * j], l[2 * j]);
-                            split_tf32(X * b[j].y, h[2 * j + 1], l[2 * j + 1]);
-                        }
-#pragma unroll
-                        for (int c = 0; c < 2; c++) {
-                            const uint32_t o = tc::operand_offset(row, 16 * c);
-                            st16(stg + 4 * A_BYTES + o, h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
-                            st16(stg + 4 * A_BYTES + B_BYTES + o, l[4 * c], l[4 * c + 1], l[4 * c + 2], l[4 * c + 3]);
-                        }
+                    unsigned char *bh = stg + 2 * A_BYTES, *blo = bh + B_BYTES;
+                    st16(bh + o_row + 16 * x, h[0], h[1], h[2], h[3]);
+                    st16(blo + o_row + 16 * x, l[0], l[1], l[2], l[3]);
+                    if (TF32) {   // (re, im) -> (-im, re)
+                        st16(bh + o_im + 16 * x, h[1] ^ 0x80000000u, h[0], h[3] ^ 0x80000000u, h[2]);
+                        st16(blo + o_im + 16 * x, l[1] ^ 0x80000000u, l[0], l[3] ^ 0x80000000u, l[2]);
                     } else {
-                        uint32_t h[4], l[4];
-#pragma unroll
-                        for (int j = 0; j < 4; j++) {
-                            const float X = x ? cur.xs[j].y : cur.xs[j].x;
-                            split_bf16(X * b[j].x, X * b[j].y, h[j], l[j]);
-                        }
-                        const uint32_t o = tc::operand_offset(row, 16 * pr.hB);
-                        st16(stg + 4 * A_BYTES + o, h[0], h[1], h[2], h[3]);
-                        st16(stg + 4 * A_BYTES + B_BYTES + o, l[0], l[1], l[2], l[3]);
+                        st16(bh + o_im + 16 * x, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
+                        st16(blo + o_im + 16 * x, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
                     }
                 }
             }
+        };
+        // one pipeline step: prefetch the next stage, wait for the slot
+        // (draining a finished segment meanwhile), form the operands
+        auto step = [&](int it, const Pre &use, Pre &next) -> bool {
+            if (it + 1 < nstg) load(it + 1, next);
+            const int slot = it % NST;
+            const uint32_t par = ((it / NST) & 1) ^ 1;
+            const uint64_t t0 = tc::global_ns();
+            for (uint32_t i = 0;; i++) {
+                // a completed phase stays complete until this slot is refilled,
+                // so the lanes agree once all have seen it
+                if (__all_sync(0xffffffffu, tc::mbar_try_wait_sleep(&empty[slot], par, isA ? 1000u : 20000u))) break;
+                if (isA && ready()) drain();
+                if ((i & 63) == 63 &&
+                    __any_sync(0xffffffffu, abort_flag != 0 || tc::global_ns() - t0 > 2000000000ull))
+                    return false;
+            }
+            produce(it, use);
             tc::fence_async_smem();
             tc::mbar_arrive(&full[slot]);
-            cur = nxt;
+            // a segment can only have finished once its last stage was formed
+            if (isA && it >= (nd + 1) * SEG && ready()) drain();
+            return true;
+        };
+        Pre b0, b1;
+        if (nstg > 0) load(0, b0);
+        bool ok = true;
+        for (int it = 0; it < nstg && ok; it += 2) {
+            ok = step(it, b0, b1);
+            if (ok && it + 1 < nstg) ok = step(it + 1, b1, b0);
         }
+        if (isA) {
+            // the remaining segments
+            while (ok && nd < nseg) {
+                const bool got =
+                    __all_sync(0xffffffffu, tc::mbar_wait(&seg_full[nd & 1], (nd >> 1) & 1, &abort_flag));
+                if (!got) ok = false;
+                else drain();
+            }
+        }
+        if (!ok) abort_flag = 1;
+        ok = __all_sync(0xffffffffu, ok && abort_flag == 0);
+        if (!ok && lane == 0) atomicOr(&P.status->err[EC_RUN], EB_TIMEOUT);
 
         // ------------------------------------------------------------ epilogue
-        bool ok = abort_flag == 0;
-        if (ok && nstg > 0) ok = tc::mbar_wait(&done, 0, &abort_flag);
-        ok = __all_sync(0xffffffffu, ok);
-        tc::tc_fence_after();
-        if (ok) {
-            const int quad = warp & 3, qh = warp >> 2;
-            const int p = 32 * quad + lane, pgl = p0 + p;
+        // A warps: row p = lrow against q = 16 half .. 16 half + 15, from this
+        // thread's own running sums
+        if (ok && isA) {
+            const int pgl = p0 + lrow;
             const bool prow = pgl < P.na;
             float2 gp[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
             if (P.has_gains && prow) {
-                const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + pgl) * P.nchan + k));
+                const float4 *g4 =
+                    reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + pgl) * P.nchan + k));
                 const float4 a01 = g4[0], a23 = g4[1];
                 gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
                 gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
             }
-            const uint32_t lane_addr = tmem + ((uint32_t)(32 * quad) << 16);
-            for (int qq = 0; qq < 32; qq += 2) {
-                const int ql = 32 * qh + qq;
-                uint32_t re[8] = {0, 0, 0, 0, 0, 0, 0, 0}, im[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                if (nstg > 0) {
-                    tc::tmem_ld8(lane_addr + 4 * ql, re);
-                    tc::tmem_ld8(lane_addr + 256 + 4 * ql, im);
-                    tc::tmem_wait_ld(re);
-                    tc::tmem_wait_ld(im);
+            const long long rowbase = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 - pgl - 1;
+#pragma unroll 2
+            for (int i = 0; i < 16; i++) {
+                const int ql = 16 * half + i, q = q0 + ql;
+                if (!(prow && pgl < q && q < P.na)) continue;
+                float Sv[8];   // Re I, Q, U, V then Im I, Q, U, V
+#pragma unroll
+                for (int x = 0; x < 4; x++) {
+                    Sv[x] = nseg > 0 ? totals[(4 * ql + x) * 128 + lrow] : 0.f;
+                    Sv[4 + x] = nseg > 0 ? totals[(128 + 4 * ql + x) * 128 + lrow] : 0.f;
                 }
+                float2 Sm[4];
+                Sm[0] = make_float2(Sv[0] + Sv[1], Sv[4] + Sv[5]);   // I + Q
+                Sm[1] = make_float2(Sv[2] - Sv[7], Sv[6] + Sv[3]);   // U + iV
+                Sm[2] = make_float2(Sv[2] + Sv[7], Sv[6] - Sv[3]);   // U - iV
+                Sm[3] = make_float2(Sv[0] - Sv[1], Sv[4] - Sv[5]);   // I - Q
+                float2 gq[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
+                if (P.has_gains) {
+                    const float4 *g4 =
+                        reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
+                    const float4 b01 = g4[0], b23 = g4[1];
+                    gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
+                    gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
+                }
+                float2 V[4], tmp[4], gqh[4];
+                mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
+                mherm(gq, gqh);
+                mmul(tmp, gqh, V);
+                const long long vrow = ((long long)t * P.nbl + rowbase + q) * P.nchan + k;
+                if (WRITE) {
+                    float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * vrow);
+                    o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
+                    o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
+                } else {
+                    const float4 *d4 = reinterpret_cast<const float4 *>(P.data + 4 * vrow);
+                    const float4 d01 = d4[0], d23 = d4[1];
+                    const float2 D[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w),
+                                         make_float2(d23.x, d23.y), make_float2(d23.z, d23.w)};
+                    float r2 = 0.f;
 #pragma unroll
-                for (int i = 0; i < 2; i++) {
-                    const int q = q0 + ql + i;
-                    if (!(prow && pgl < q && q < P.na)) continue;
-                    const float Ir = __uint_as_float(re[4 * i]), Ii = __uint_as_float(im[4 * i]);
-                    const float Qr = __uint_as_float(re[4 * i + 1]), Qi = __uint_as_float(im[4 * i + 1]);
-                    const float Ur = __uint_as_float(re[4 * i + 2]), Ui = __uint_as_float(im[4 * i + 2]);
-                    const float Vr = __uint_as_float(re[4 * i + 3]), Vi = __uint_as_float(im[4 * i + 3]);
-                    float2 Sm[4];
-                    Sm[0] = make_float2(Ir + Qr, Ii + Qi);   // I + Q
-                    Sm[1] = make_float2(Ur - Vi, Ui + Vr);   // U + iV
-                    Sm[2] = make_float2(Ur + Vi, Ui - Vr);   // U - iV
-                    Sm[3] = make_float2(Ir - Qr, Ii - Qi);   // I - Q
-                    float2 gq[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
-                    if (P.has_gains) {
-                        const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
-                        const float4 b01 = g4[0], b23 = g4[1];
-                        gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
-                        gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
+                    for (int c = 0; c < 4; c++) {
+                        const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
+                        r2 += dr * dr + di * di;
                     }
-                    float2 V[4], tmp[4], gqh[4];
-                    mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
-                    mherm(gq, gqh);
-                    mmul(tmp, gqh, V);
-                    const long long bl = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 + (q - pgl - 1);
-                    const long long row = ((long long)t * P.nbl + bl) * P.nchan + k;
-                    if (WRITE) {
-                        float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * row);
-                        o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
-                        o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
-                    } else {
-                        const float4 *d4 = reinterpret_cast<const float4 *>(P.data + 4 * row);
-                        const float4 d01 = d4[0], d23 = d4[1];
-                        const float2 D[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w),
-                                             make_float2(d23.x, d23.y), make_float2(d23.z, d23.w)};
-                        float r2 = 0.f;
-#pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
-                            r2 += dr * dr + di * di;
-                        }
-                        const float w = P.has_weight ? P.weight[row] : 1.f;
-                        chi += (double)(w * r2);
-                    }
+                    const float w = P.has_weight ? P.weight[vrow] : 1.f;
+                    chi += (double)(w * r2);
                 }
             }
-        } else {
-            atomicOr(&P.status->err[EC_RUN], EB_TIMEOUT);
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         const uint32_t idesc = tc::instr_desc(TF32 ? tc::kFmtTF32 : tc::kFmtBF16, PT, NB);
         const uint32_t sbase = tc::smem_u32(smem);
         for (int it = 0; it < nstg; it++) {
+            const int g = it / SEG, b = g & 1, first = it % SEG == 0;
+            if (first && g >= 2 && !tc::mbar_wait(&seg_empty[b], ((g >> 1) - 1) & 1, &abort_flag)) {
+                abort_flag = 1;
+                break;
+            }
             const int slot = it % NST;
             if (!tc::mbar_wait(&full[slot], (it / NST) & 1, &abort_flag)) {
                 abort_flag = 1;
@@ -402,24 +428,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
             }
             tc::tc_fence_after();
             const uint32_t sb = sbase + slot * STAGE_BYTES;
-            const uint64_t bh = tc::smem_desc(sb + 4 * A_BYTES), bl = tc::smem_desc(sb + 4 * A_BYTES + B_BYTES);
-#pragma unroll
-            for (int h = 0; h < 2; h++) {   // h = 0: Re S (A), h = 1: Im S (-i A)
-                const uint64_t ah = tc::smem_desc(sb + 2 * h * A_BYTES), alo = tc::smem_desc(sb + (2 * h + 1) * A_BYTES);
-                const uint32_t d = tmem + 256 * h;
-                if (TF32) {
-                    tc::mma_tf32(d, ah, bh, idesc, it > 0);
-                    tc::mma_tf32(d, ah, bl, idesc, 1);
-                    tc::mma_tf32(d, alo, bh, idesc, 1);
-                } else {
-                    tc::mma_bf16(d, ah, bh, idesc, it > 0);
-                    tc::mma_bf16(d, ah, bl, idesc, 1);
-                    tc::mma_bf16(d, alo, bh, idesc, 1);
-                }
+            const uint64_t ah = tc::smem_desc(sb), alo = tc::smem_desc(sb + A_BYTES);
+            const uint64_t bh = tc::smem_desc(sb + 2 * A_BYTES), bl = tc::smem_desc(sb + 2 * A_BYTES + B_BYTES);
+            const uint32_t d = tmem + 256 * b;   // columns: Re S (B rows 0-127), Im S (rows 128-255)
+            if (TF32) {
+                tc::mma_tf32(d, alo, bh, idesc, !first);
+                tc::mma_tf32(d, ah, bl, idesc, 1);
+                tc::mma_tf32(d, ah, bh, idesc, 1);
+            } else {
+                tc::mma_bf16(d, alo, bh, idesc, !first);
+                tc::mma_bf16(d, ah, bl, idesc, 1);
+                tc::mma_bf16(d, ah, bh, idesc, 1);
             }
             tc::mma_commit(&empty[slot]);
+            if (it % SEG == SEG - 1 || it == nstg - 1) tc::mma_commit(&seg_full[b]);
         }
-        tc::mma_commit(&done);
     }
 
     // ---------------------------------------------------------------- teardown
@@ -464,15 +487,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
 // Per-source factors of the B operand for each (t, k): the Stokes vector
 // times the spectral factor (nu/nu_ref)^alpha (eq. 2) and, without pointing
 // errors, times the beam of both antennas E_s^2 (eq. 4; the same for every
-// antenna). out [trows][nchan][nsrc][4].
-__global__ void k_split_scales(int nsrc, int nchan, int trows, int na, const ChanF *chan, const float *stokes,
-                               const float *alpha, const float *rho, int pointing, float4 *out) {
-    const long long n = (long long)trows * nchan * nsrc;
+// antenna). out [trows][nchan][nsrc_pad][4], zero for s >= nsrc.
+__global__ void k_split_scales(int nsrc, int nsrc_pad, int nchan, int trows, int na, const ChanF *chan,
+                               const float *stokes, const float *alpha, const float *rho, int pointing, float4 *out) {
+    const long long n = (long long)trows * nchan * nsrc_pad;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)(i % nsrc);
-        const long long r = i / nsrc;
+        const int s = (int)(i % nsrc_pad);
+        const long long r = i / nsrc_pad;
         const int k = (int)(r % nchan);
         const int t = (int)(r / nchan);
+        if (s >= nsrc) {
+            out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         const ChanF ch = chan[k];
         float f = exp2f(2.0f * alpha[s] * ch.hlr);
         if (!pointing) {
@@ -537,7 +564,8 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
     e = reset_status_class(c, EC_MODE);
     if (e != cudaSuccess) return e;
     const int trows = c->time_varying ? c->dims.ntime : 1;
-    const size_t nscale = (size_t)trows * c->dims.nchan * c->nsrc;
+    const int nsrc_pad = (c->nsrc + 7) / 8 * 8;
+    const size_t nscale = (size_t)trows * c->dims.nchan * nsrc_pad;
     if (nscale > c->sscale_cap) {
         if (c->d_sscale) cudaFree(c->d_sscale);
         c->d_sscale = nullptr;
@@ -552,7 +580,7 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int nb = (int)std::min<size_t>((nscale + 255) / 256, 4096);
-        k_split_scales<<<nb, 256, 0, c->stream>>>(c->nsrc, c->dims.nchan, trows, c->dims.na,
+        k_split_scales<<<nb, 256, 0, c->stream>>>(c->nsrc, nsrc_pad, c->dims.nchan, trows, c->dims.na,
                                                   reinterpret_cast<const ChanF *>(c->d_chan),
                                                   reinterpret_cast<const float *>(c->d_stokes),
                                                   reinterpret_cast<const float *>(c->d_alpha),
@@ -577,6 +605,7 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
     P.rho = reinterpret_cast<const float *>(c->d_rho);
     P.scale = reinterpret_cast<const float *>(c->d_sscale);
     P.scale_trows = trows;
+    P.nsrc_pad = nsrc_pad;
     P.gains = reinterpret_cast<const float2 *>(c->d_gains);
     P.data = reinterpret_cast<const float2 *>(c->d_data);
     P.weight = reinterpret_cast<const float *>(c->d_weight);
