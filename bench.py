@@ -42,6 +42,24 @@ def peak_fp32_tflops(mhz):
     return 2.0 * FP32_LANES_PER_SM * SM_COUNT * mhz * 1e6 / 1e12
 
 
+def profiled_traffic():
+    """DRAM bytes per launch of the fused chi^2 kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", "fused_chi2_fp32_64ant.md")).read()
+        src = open(os.path.join(ROOT, "paper_1501_07719_gb300", "csrc", "rime_fused.cu"), "rb").read()
+    except OSError:
+        return None
+    vals = dict(line.split(": ", 1) for line in text.splitlines()
+                if line.startswith(("traffic_bytes_per_launch: ", "source_md5: ")))
+    if "traffic_bytes_per_launch" not in vals or "source_md5" not in vals:
+        return None
+    if not vals["source_md5"].startswith(hashlib.md5(src).hexdigest()[:12]):
+        return None
+    return int(vals["traffic_bytes_per_launch"])
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -279,13 +297,63 @@ def form_split(torch, R):
                      "chi2_rel_err_vs_fp64": abs(chi_sl - chi_ref) / chi_ref}
     ctx.close()
     csl.close()
-    for name in ("split_bf16", "split_tf32"):
+    # roofline of the split kernels: algorithmic tensor flops = the real products
+    # the baselines need (nbl x nsrc x 4 Stokes x 2 parts x K=2 per source x 2
+    # flops) times the three split products, against the measured sustained
+    # BF16 peak (TF32: times the nominal TF32/BF16 ratio 1.1/2.25)
+    pk = measured_peaks()
+    bf16_peak = pk.get("bf16_tflops_sustained", 1700.0)
+    algo = wl.ntime * wl.nchan * wl.nbl * wl.nsrc * 4 * 2 * 2 * 2 * 3
+    for name, peak in (("split_bf16", bf16_peak), ("split_tf32", bf16_peak * 1.1 / 2.25)):
         res[name]["speedup_vs_direct"] = res["direct_fp32"]["ms"] / res[name]["ms"]
+        ach = algo / (res[name]["ms"] * 1e-3) / 1e12
+        res[name]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": ach / peak,
+                                 "peak_basis": "MEASURED_PEAKS.json bf16_tflops_sustained"
+                                 + (" x 1.1/2.25 (nominal TF32/BF16)" if name == "split_tf32" else "")}
     res["workload"] = wl.name
     res["terms_per_s"] = {kk: terms_of(wl) / (v["ms"] * 1e-3) for kk, v in res.items() if isinstance(v, dict)}
     res["errors"] = ("vis: max |V - V_fp64| / max |V_fp64| over 64 sampled (t, baseline, channel); "
                      "chi2: |chi2 - chi2_fp64| / chi2_fp64 on timestep 0, channels 0-1, data = model + noise")
     return res
+
+
+def run_only(args):
+    """One form on one (possibly reduced) workload, for profiling: prints the
+    median launch time. Not the benchmark line."""
+    import torch
+    import paper_1501_07719_gb300 as R
+    over = {k: v for k, v in (("ntime", args.ntime), ("nchan", args.nchan)) if v}
+    wl = rime_synth.workload(args.workload, **over)
+    inp = rime_synth.make_inputs(wl, precision="f32")
+    w = inp["weight"].astype(np.float32)
+    stream = torch.cuda.current_stream()
+    ctx = R.Rime(inp, R.RIME_FP32, weight=w, stream=stream)
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])
+    V = ctx.predict()
+    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64), w)
+    del V
+    out = torch.zeros(max(1, wl.nsets), dtype=torch.float64, device="cuda")
+    if args.only in ("chi2", "split-bf16", "split-tf32"):
+        ctx.set_tensor_mode({"chi2": R.RIME_TC_OFF, "split-bf16": R.RIME_TC_SPLIT_BF16,
+                             "split-tf32": R.RIME_TC_SPLIT_TF32}[args.only])
+        fn = lambda: ctx.chi2_async(out)
+    elif args.only == "grad":
+        gs = torch.zeros((wl.nsrc, 10), dtype=torch.float64, device="cuda")
+        gg = torch.zeros((wl.ntime, wl.na, wl.nchan, 2, 2), dtype=torch.complex128, device="cuda")
+        fn = lambda: R.rime_chi2_grad(ctx.ctx, gs, gg)
+    else:
+        sets = inp["sets"]
+        fn = lambda: ctx.chi2_batched(sets["offsets"], sets["sources"], out=out)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = _timed(torch, stream, fn, args.steps)
+    ctx.close()
+    print(json.dumps({"only": args.only, "workload": wl.name, "ntime": wl.ntime, "nchan": wl.nchan,
+                      "median_ms": ms}), flush=True)
+    return 0
 
 
 def run_reference(args, wl, rank, world):
@@ -326,7 +394,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the gradient, batched and split-precision comparisons")
+    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32"],
+                    help="time one form on --workload (optionally with fewer timesteps / channels) "
+                         "instead of the benchmark; for profiling")
+    ap.add_argument("--ntime", type=int, default=0)
+    ap.add_argument("--nchan", type=int, default=0)
     args = ap.parse_args()
+    if args.only:
+        return run_only(args)
     wl = rime_synth.WORKLOADS[args.workload]
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
@@ -434,7 +509,8 @@ def main():
                    "parallelism": f"replicas x{world} (time chunks)" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "kernel": "k_fused<float, chi2>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic() if args.workload == WORKLOAD else None,
+                     "traffic_unit": "bytes per launch (ncu dram read + write, profiles/fused_chi2_fp32_64ant.md)",
                      "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz",
                      "algorithmic": f"{FLOPS_POINT} flops/point term, {FLOPS_GAUSS}/Gaussian term",
                      "avg_launch_ms": avg_launch_s * 1e3},
