@@ -404,14 +404,15 @@ struct Smem {
 
 // Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
 // nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small
-// products add the rest; the result is reduced to about [-1/2, 1/2] turns.
+// products add the rest; the result is reduced to about [-1/2, 1/2] turns,
+// where the SFU sine and cosine are accurate to ~2^-21 absolute.
 __device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
     float p = ch.nu_hi * tau.x;
     float e = fmaf(ch.nu_hi, tau.x, -p);
     float r = p - round_int_f(p);
     float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
     float sn, cs;
-    sincospif(2.0f * f, &sn, &cs);
+    __sincosf(6.28318530717958648f * f, &sn, &cs);
     return make_float2(cs, sn);
 }
 

@@ -28,15 +28,17 @@
 // sources straight into shared memory: the phase nu tau is reduced exactly in
 // double-float arithmetic (the delays tau come from the FP64 upload kernel)
 // and its sine and cosine are taken with the SFU; one thread issues the
-// MMAs; a three-stage mbarrier pipeline connects them.
+// MMAs; an eight-stage mbarrier pipeline connects them.
 //
 // The tensor core adds each MMA's products into its FP32 accumulator with
 // truncation, losing about one unit in the last place of the running sum per
 // MMA, a bias toward zero that grows with the number of MMAs into one
 // accumulator. So the accumulators (Re and Im, 128 columns each) live in two
 // TMEM buffers used in turn for segments of eight stages: while the MMAs fill
-// one, the producer warps add the other into FP32 running sums in shared
-// memory (round to nearest). The epilogue applies the Stokes combination
+// one, the A producer warps add the other into FP32 running sums held in
+// their registers (round to nearest; the warpgroups' register budgets are
+// rebalanced with setmaxnreg so that each A thread can hold its 128 sums).
+// The epilogue applies the Stokes combination
 // (eq. 2) and the gains (eq. 1) to the running sums and writes V or forms
 // w |V - D|^2 (eq. 7), summed in FP64.
 #include "rime_internal.cuh"
@@ -54,15 +56,19 @@ constexpr int QT = 32;                  // column antennas per tile
 constexpr int NB = 8 * QT;              // B rows: (q, X) for Re S, then i (q, X) for Im S; MMA N
 constexpr int NDRAIN = 256;             // A producers, which also drain and run the epilogue
 constexpr int NPROD = NDRAIN + 128;     // and four warps of B producers
-constexpr int THREADS = NPROD + 32;     // and one MMA warp
-constexpr int NST = 3;                  // pipeline stages
+constexpr int THREADS = NPROD + 128;    // and a warpgroup whose first warp issues the MMAs
+constexpr int NST = 8;                  // pipeline stages
+// registers per thread: at launch (65536 / THREADS), then per warpgroup
+// A (two warpgroups: 128 running sums each), B, MMA: 2*128*200 + 128*88 +
+// 128*24 = 65536 = 128 * 512
+constexpr int REGS_LAUNCH = 128, REGS_A = 200, REGS_B = 88, REGS_MMA = 24;
+static_assert(2 * 128 * REGS_A + 128 * REGS_B + 128 * REGS_MMA <= REGS_LAUNCH * THREADS, "register split");
 constexpr int SEG = 8;                  // stages accumulated in TMEM before a drain
 constexpr uint32_t A_BYTES = tc::operand_bytes(PT);
 constexpr uint32_t B_BYTES = tc::operand_bytes(NB);
 // one stage: A hi, A lo, B hi, B lo
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-// + FP32 running sums of the accumulators: 256 columns x 128 rows
-constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES + 256 * 128 * 4;
+constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 512;     // two buffers of (Re, Im) x 128 columns
 static_assert(SMEM_BYTES + 1024 <= 227 * 1024, "shared memory");
 static_assert(STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "operand alignment");
@@ -133,7 +139,7 @@ __device__ __forceinline__ void st16(unsigned char *p, uint32_t a, uint32_t b, u
 // sits at K index 2 j + c. Warps 0-7 form A (thread: row p, chunk), drain
 // the accumulators and run the epilogue; warps 8-11 form B (thread: antenna
 // q, chunk and a pair of Stokes parameters: rows (q, X) and i (q, X) from one
-// phase); warp 12 issues the MMAs. Sources past the end read the last source's delays and
+// phase); warp 12 issues the MMAs; warps 13-15 only lend their registers. Sources past the end read the last source's delays and
 // meet a zero Stokes scale, so they add nothing; rows and columns past the
 // last antenna are never read back.
 template <bool TF32>
@@ -142,9 +148,341 @@ struct Item {
     static constexpr int SPS = 2 * SPC;        // sources per stage
 };
 
+// State shared by the roles of one CTA.
+struct Cta {
+    const SplitParams &P;
+    unsigned char *smem;
+    uint64_t *full, *empty, *seg_full, *seg_empty;
+    int *abort_flag;
+    uint32_t tmem;
+    int t, k, p0, q0, nstg, nseg;
+    ChanF ch;
+};
+
+// Inputs of one chunk of one producer thread, loaded a stage ahead (beam
+// radii, needed only with pointing errors, are loaded where used).
+template <int SPC>
+struct Pre {
+    float2 tau[SPC];
+    float2 x[SPC];   // B: the Stokes pair (X = 2 xp, 2 xp + 1) of each source
+};
+
+// Waits for pipeline slot `it` to be free; A warps drain finished segments
+// meanwhile. Warp-uniform; false when the block gave up.
+template <typename Drain>
+__device__ __forceinline__ bool wait_slot(const Cta &C, int it, int lane, Drain &&maybe_drain) {
+    const int slot = it % NST;
+    const uint32_t par = ((it / NST) & 1) ^ 1;
+    const uint64_t t0 = tc::global_ns();
+    for (uint32_t i = 0;; i++) {
+        // a completed phase stays complete until this slot is refilled, so
+        // the lanes agree once all have seen it
+        if (__all_sync(0xffffffffu, tc::mbar_try_wait_sleep(&C.empty[slot], par, 1000u))) return true;
+        maybe_drain();
+        if ((i & 63) == 63 &&
+            __any_sync(0xffffffffu, *(volatile int *)C.abort_flag != 0 || tc::global_ns() - t0 > 2000000000ull))
+            return false;
+    }
+}
+
+// Warps 0-7: A = E K rows (row p, chunk), the drains into register sums, and
+// the epilogue. Returns this thread's chi^2 contribution.
+template <bool TF32, bool WRITE>
+__device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int lane) {
+    constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
+    const SplitParams &P = C.P;
+    const int row = tid & 127, chunk = tid >> 7;
+    const int ant = min(C.p0 + row, P.na - 1);
+    const long long tbase = (long long)C.t * P.nsrc * P.na + ant;
+    const uint32_t o_row = tc::operand_offset(row, 16 * chunk);
+    const bool pointing = P.has_pointing != 0;
+    const int quad = warp & 3, half = (warp >> 2) & 1;
+    const int lrow = 32 * quad + lane;
+    const ChanF ch = C.ch;
+
+    auto load = [&](int it, Pre<SPC> &L) {
+        const int sb = it * SPS + chunk * SPC;
+#pragma unroll
+        for (int j = 0; j < SPC; j++) L.tau[j] = P.tau[tbase + (long long)min(sb + j, P.nsrc - 1) * P.na];
+    };
+    // FP32 running sums of this thread's accumulator columns: Re S then Im S
+    // for columns 64 half .. 64 half + 63 of each
+    float tot[128];
+#pragma unroll
+    for (int c = 0; c < 128; c++) tot[c] = 0.f;
+    int nd = 0;   // next segment to drain
+    auto drain = [&]() {
+        const int b = nd & 1;
+        tc::tc_fence_after();
+#pragma unroll
+        for (int h = 0; h < 2; h++)   // Re, Im
+#pragma unroll
+            for (int c4 = 0; c4 < 4; c4++) {
+                uint32_t r[16];
+                const int col0 = 128 * h + 64 * half + 16 * c4;
+                tc::tmem_ld16(C.tmem + ((uint32_t)(32 * quad) << 16) + 256 * b + col0, r);
+                tc::tmem_wait_ld16(r);
+#pragma unroll
+                for (int c = 0; c < 16; c++) tot[64 * h + 16 * c4 + c] += __uint_as_float(r[c]);
+            }
+        tc::tc_fence_before();
+        tc::mbar_arrive(&C.seg_empty[b]);
+        nd++;
+    };
+    // warp-uniform: drain the next segment if it is complete
+    auto maybe_drain = [&]() {
+        bool r = false;
+        if (lane == 0) r = nd < C.nseg && tc::mbar_try_wait(&C.seg_full[nd & 1], (nd >> 1) & 1);
+        if (__shfl_sync(0xffffffffu, r, 0)) drain();
+    };
+    auto produce = [&](int it, const Pre<SPC> &L) {
+        unsigned char *stg = C.smem + (it % NST) * STAGE_BYTES;
+        float2 a[SPC];
+#pragma unroll
+        for (int j = 0; j < SPC; j++) {
+            a[j] = phase_sfu(L.tau[j], ch);
+            if (pointing) {
+                const int s = min(it * SPS + chunk * SPC + j, P.nsrc - 1);
+                const float E = beam_f(P.rho[tbase + (long long)s * P.na], ch);
+                a[j].x *= E;
+                a[j].y *= E;
+            }
+        }
+        uint32_t h[4], l[4];
+        if (TF32) {
+#pragma unroll
+            for (int j = 0; j < SPC; j++) {
+                split_tf32(a[j].x, h[2 * j], l[2 * j]);
+                split_tf32(a[j].y, h[2 * j + 1], l[2 * j + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < SPC; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
+        }
+        st16(stg + o_row, h[0], h[1], h[2], h[3]);
+        st16(stg + A_BYTES + o_row, l[0], l[1], l[2], l[3]);
+    };
+    auto step = [&](int it, const Pre<SPC> &use, Pre<SPC> &next) -> bool {
+        if (it + 1 < C.nstg) load(it + 1, next);
+        if (!wait_slot(C, it, lane, maybe_drain)) return false;
+        produce(it, use);
+        tc::fence_async_smem();
+        tc::mbar_arrive(&C.full[it % NST]);
+        // a segment can only have finished once its last stage was formed
+        if (it >= (nd + 1) * SEG) maybe_drain();
+        return true;
+    };
+    Pre<SPC> b0, b1;
+    if (C.nstg > 0) load(0, b0);
+    bool ok = true;
+    for (int it = 0; it < C.nstg && ok; it += 2) {
+        ok = step(it, b0, b1);
+        if (ok && it + 1 < C.nstg) ok = step(it + 1, b1, b0);
+    }
+    while (ok && nd < C.nseg) {   // the remaining segments
+        const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&C.seg_full[nd & 1], (nd >> 1) & 1, C.abort_flag));
+        if (!got) ok = false;
+        else drain();
+    }
+    if (!ok) *(volatile int *)C.abort_flag = 1;
+    ok = __all_sync(0xffffffffu, ok && *(volatile int *)C.abort_flag == 0);
+    if (!ok) {
+        if (lane == 0) atomicOr(&P.status->err[EC_RUN], EB_TIMEOUT);
+        return 0.0;
+    }
+
+    // ---- epilogue: row p = lrow against q = 16 half .. 16 half + 15 ----
+    // Every MMA has completed and every stage has been consumed, so the stage
+    // buffers take this thread's sums ([256 columns][128 rows]); each thread
+    // reads back only what it wrote.
+    float *ts = reinterpret_cast<float *>(C.smem);
+#pragma unroll
+    for (int c = 0; c < 64; c++) {
+        ts[(64 * half + c) * 128 + lrow] = tot[c];
+        ts[(128 + 64 * half + c) * 128 + lrow] = tot[64 + c];
+    }
+    double chi = 0.0;
+    const int pgl = C.p0 + lrow;
+    const bool prow = pgl < P.na;
+    const int t = C.t, k = C.k;
+    float2 gp[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
+    if (P.has_gains && prow) {
+        const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + pgl) * P.nchan + k));
+        const float4 a01 = g4[0], a23 = g4[1];
+        gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
+        gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
+    }
+    const long long rowbase = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 - pgl - 1;
+#pragma unroll 1
+    for (int i = 0; i < 16; i++) {
+        const int q = C.q0 + 16 * half + i;
+        if (!(prow && pgl < q && q < P.na)) continue;
+        float Sv[8];   // Re I, Q, U, V then Im I, Q, U, V
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            Sv[x] = ts[(64 * half + 4 * i + x) * 128 + lrow];
+            Sv[4 + x] = ts[(128 + 64 * half + 4 * i + x) * 128 + lrow];
+        }
+        float2 Sm[4];
+        Sm[0] = make_float2(Sv[0] + Sv[1], Sv[4] + Sv[5]);   // I + Q
+        Sm[1] = make_float2(Sv[2] - Sv[7], Sv[6] + Sv[3]);   // U + iV
+        Sm[2] = make_float2(Sv[2] + Sv[7], Sv[6] - Sv[3]);   // U - iV
+        Sm[3] = make_float2(Sv[0] - Sv[1], Sv[4] - Sv[5]);   // I - Q
+        float2 gq[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
+        if (P.has_gains) {
+            const float4 *g4 = reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
+            const float4 b01 = g4[0], b23 = g4[1];
+            gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
+            gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
+        }
+        float2 V[4], tmp[4], gqh[4];
+        mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
+        mherm(gq, gqh);
+        mmul(tmp, gqh, V);
+        const long long vrow = ((long long)t * P.nbl + rowbase + q) * P.nchan + k;
+        if (WRITE) {
+            float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * vrow);
+            o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
+            o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
+        } else {
+            const float4 *d4 = reinterpret_cast<const float4 *>(P.data + 4 * vrow);
+            const float4 d01 = d4[0], d23 = d4[1];
+            const float2 D[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w),
+                                 make_float2(d23.x, d23.y), make_float2(d23.z, d23.w)};
+            float r2 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
+                r2 += dr * dr + di * di;
+            }
+            const float w = P.has_weight ? P.weight[vrow] : 1.f;
+            chi += (double)(w * r2);
+        }
+    }
+    return chi;
+}
+
+// Warps 8-11: B rows (antenna q, chunk, Stokes pair xp): X A_q and i X A_q
+// for X = 2 xp, 2 xp + 1, from one phase per (q, source).
+template <bool TF32>
+__device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
+    constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
+    const SplitParams &P = C.P;
+    const int bw = warp - NDRAIN / 32;
+    const int chunk = bw & 1, xp = bw >> 1;
+    const int row = lane;
+    const int ant = min(C.q0 + row, P.na - 1);
+    const long long tbase = (long long)C.t * P.nsrc * P.na + ant;
+    const float2 *scale = reinterpret_cast<const float2 *>(P.scale) +
+                          2 * ((long long)(P.scale_trows > 1 ? C.t : 0) * P.nchan * P.nsrc_pad + (long long)C.k * P.nsrc_pad);
+    const uint32_t o_re = tc::operand_offset(4 * row + 2 * xp, 16 * chunk);
+    const uint32_t o_im = tc::operand_offset(4 * QT + 4 * row + 2 * xp, 16 * chunk);
+    const bool pointing = P.has_pointing != 0;
+    const ChanF ch = C.ch;
+
+    auto load = [&](int it, Pre<SPC> &L) {
+        const int sb = it * SPS + chunk * SPC;
+#pragma unroll
+        for (int j = 0; j < SPC; j++) {
+            L.tau[j] = P.tau[tbase + (long long)min(sb + j, P.nsrc - 1) * P.na];
+            L.x[j] = scale[2 * (sb + j) + xp];   // zero past the last source
+        }
+    };
+    auto produce = [&](int it, const Pre<SPC> &L) {
+        unsigned char *bh = C.smem + (it % NST) * STAGE_BYTES + 2 * A_BYTES, *blo = bh + B_BYTES;
+        float2 a[SPC];
+#pragma unroll
+        for (int j = 0; j < SPC; j++) {
+            a[j] = phase_sfu(L.tau[j], ch);
+            if (pointing) {
+                const int s = min(it * SPS + chunk * SPC + j, P.nsrc - 1);
+                const float E = beam_f(P.rho[tbase + (long long)s * P.na], ch);
+                a[j].x *= E;
+                a[j].y *= E;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 2; x++) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int j = 0; j < SPC; j++) {
+                const float X = x == 0 ? L.x[j].x : L.x[j].y;
+                if (TF32) {
+                    split_tf32(X * a[j].x, h[2 * j], l[2 * j]);
+                    split_tf32(X * a[j].y, h[2 * j + 1], l[2 * j + 1]);
+                } else {
+                    split_bf16(X * a[j].x, X * a[j].y, h[j], l[j]);
+                }
+            }
+            st16(bh + o_re + 16 * x, h[0], h[1], h[2], h[3]);
+            st16(blo + o_re + 16 * x, l[0], l[1], l[2], l[3]);
+            if (TF32) {   // (re, im) -> (-im, re)
+                st16(bh + o_im + 16 * x, h[1] ^ 0x80000000u, h[0], h[3] ^ 0x80000000u, h[2]);
+                st16(blo + o_im + 16 * x, l[1] ^ 0x80000000u, l[0], l[3] ^ 0x80000000u, l[2]);
+            } else {
+                st16(bh + o_im + 16 * x, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
+                st16(blo + o_im + 16 * x, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
+            }
+        }
+    };
+    auto no_drain = [] {};
+    Pre<SPC> b0, b1;
+    if (C.nstg > 0) load(0, b0);
+    bool ok = true;
+    for (int it = 0; it < C.nstg && ok; it += 2) {
+        for (int u = 0; u < 2 && ok && it + u < C.nstg; u++) {
+            Pre<SPC> &use = u ? b1 : b0, &next = u ? b0 : b1;
+            if (it + u + 1 < C.nstg) load(it + u + 1, next);
+            ok = wait_slot(C, it + u, lane, no_drain);
+            if (ok) {
+                produce(it + u, use);
+                tc::fence_async_smem();
+                tc::mbar_arrive(&C.full[(it + u) % NST]);
+            }
+        }
+    }
+    if (!ok) *(volatile int *)C.abort_flag = 1;
+}
+
+// Warp 12, one thread: the MMAs of each stage into the current segment's
+// TMEM buffer; commits free the stage and, at a segment's end, the buffer.
+template <bool TF32>
+__device__ __forceinline__ void role_mma(const Cta &C) {
+    const uint32_t idesc = tc::instr_desc(TF32 ? tc::kFmtTF32 : tc::kFmtBF16, PT, NB);
+    const uint32_t sbase = tc::smem_u32(C.smem);
+    for (int it = 0; it < C.nstg; it++) {
+        const int g = it / SEG, b = g & 1, first = it % SEG == 0;
+        if (first && g >= 2 && !tc::mbar_wait(&C.seg_empty[b], ((g >> 1) - 1) & 1, C.abort_flag)) {
+            *(volatile int *)C.abort_flag = 1;
+            break;
+        }
+        const int slot = it % NST;
+        if (!tc::mbar_wait(&C.full[slot], (it / NST) & 1, C.abort_flag)) {
+            *(volatile int *)C.abort_flag = 1;
+            break;
+        }
+        tc::tc_fence_after();
+        const uint32_t sb = sbase + slot * STAGE_BYTES;
+        const uint64_t ah = tc::smem_desc(sb), alo = tc::smem_desc(sb + A_BYTES);
+        const uint64_t bh = tc::smem_desc(sb + 2 * A_BYTES), bl = tc::smem_desc(sb + 2 * A_BYTES + B_BYTES);
+        const uint32_t d = C.tmem + 256 * b;   // columns: Re S (B rows 0-127), Im S (rows 128-255)
+        if (TF32) {
+            tc::mma_tf32(d, alo, bh, idesc, !first);
+            tc::mma_tf32(d, ah, bl, idesc, 1);
+            tc::mma_tf32(d, ah, bh, idesc, 1);
+        } else {
+            tc::mma_bf16(d, alo, bh, idesc, !first);
+            tc::mma_bf16(d, ah, bl, idesc, 1);
+            tc::mma_bf16(d, ah, bh, idesc, 1);
+        }
+        tc::mma_commit(&C.empty[slot]);
+        if (it % SEG == SEG - 1 || it == C.nstg - 1) tc::mma_commit(&C.seg_full[b]);
+    }
+}
+
 template <bool TF32, bool WRITE>
 __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
-    constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
+    constexpr int SPS = Item<TF32>::SPS;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t full[NST], empty[NST], seg_full[2], seg_empty[2];
     __shared__ uint32_t tmem_base;
@@ -158,11 +496,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     const int k = rest % P.nchan;
     const int t = rest / P.nchan;
     const int2 pq = P.tiles[tile];
-    const int p0 = pq.x, q0 = pq.y;
-    const ChanF ch = P.chan[k];
     const int nstg = (P.nsrc + SPS - 1) / SPS;
-    const int nseg = (nstg + SEG - 1) / SEG;
-    float *totals = reinterpret_cast<float *>(smem + NST * STAGE_BYTES);   // [256 columns][128 rows]
 
     if (tid == 0) {
         for (int i = 0; i < NST; i++) {
@@ -183,267 +517,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const uint32_t tmem = tmem_base;
+    const Cta C{P, smem, full, empty, seg_full, seg_empty, &abort_flag, tmem_base, t, k, pq.x, pq.y,
+                nstg, (nstg + SEG - 1) / SEG, P.chan[k]};
     double chi = 0.0;
-    const bool pointing = P.has_pointing != 0;
-
-    if (warp < NPROD / 32) {
-        // ------------------------------------------------------------ producers
-        const bool isA = warp < NDRAIN / 32;
-        const int bw = warp - NDRAIN / 32;                    // B warp: chunk and Stokes pair
-        const int row = isA ? (tid & 127) : lane;             // tile-local p (A) or q (B)
-        const int chunk = isA ? (tid >> 7) : (bw & 1);
-        const int xp = bw >> 1;                               // B: Stokes X = 2 xp, 2 xp + 1
-        const int ant = min((isA ? p0 : q0) + row, P.na - 1);
-        const long long tbase = (long long)t * P.nsrc * P.na + ant;
-        const float4 *scale = reinterpret_cast<const float4 *>(P.scale) +
-                              (long long)(P.scale_trows > 1 ? t : 0) * P.nchan * P.nsrc_pad + (long long)k * P.nsrc_pad;
-        const uint32_t o_row = tc::operand_offset(isA ? row : 4 * row + 2 * xp, 16 * chunk);
-        const uint32_t o_im = tc::operand_offset(4 * QT + 4 * row + 2 * xp, 16 * chunk);   // B rows of Im S
-        // drain / epilogue geometry (A warps): TMEM lanes of this warp and the
-        // 64 + 64 accumulator columns this thread owns
-        const int quad = warp & 3, half = (warp >> 2) & 1;
-        const int lrow = 32 * quad + lane;
-
-        struct Pre {
-            float2 tau[SPC];
-            float rho[SPC];
-            float4 x[SPC];
-        };
-        auto load = [&](int it, Pre &L) {
-            const int sb = it * SPS + chunk * SPC;
-#pragma unroll
-            for (int j = 0; j < SPC; j++) {
-                const int s = min(sb + j, P.nsrc - 1);
-                const long long o = tbase + (long long)s * P.na;
-                L.tau[j] = P.tau[o];
-                L.rho[j] = pointing ? P.rho[o] : 0.f;
-                if (!isA) L.x[j] = scale[sb + j];
-            }
-        };
-        int nd = 0;   // next segment to drain
-        auto drain = [&]() {
-            const int b = nd & 1;
-            tc::tc_fence_after();
-#pragma unroll
-            for (int h = 0; h < 2; h++)   // Re, Im
-#pragma unroll
-                for (int c2 = 0; c2 < 2; c2++) {
-                    uint32_t r[32];
-                    const int col0 = 128 * h + 64 * half + 32 * c2;
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * quad) << 16) + 256 * b + col0, r);
-                    tc::tmem_wait_ld32(r);
-                    float *tot = totals + col0 * 128 + lrow;
-                    if (nd == 0) {
-#pragma unroll
-                        for (int c = 0; c < 32; c++) tot[c * 128] = __uint_as_float(r[c]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 32; c++) tot[c * 128] += __uint_as_float(r[c]);
-                    }
-                }
-            tc::tc_fence_before();
-            tc::mbar_arrive(&seg_empty[b]);
-            nd++;
-        };
-        // warp-uniform: is the next segment complete?
-        auto ready = [&]() -> bool {
-            bool r = false;
-            if (lane == 0) r = nd < nseg && tc::mbar_try_wait(&seg_full[nd & 1], (nd >> 1) & 1);
-            return __shfl_sync(0xffffffffu, r, 0);
-        };
-        auto produce = [&](int it, const Pre &L) {
-            unsigned char *stg = smem + (it % NST) * STAGE_BYTES;
-            float2 a[SPC];
-#pragma unroll
-            for (int j = 0; j < SPC; j++) {
-                a[j] = phase_sfu(L.tau[j], ch);
-                if (pointing) {
-                    const float E = beam_f(L.rho[j], ch);
-                    a[j].x *= E;
-                    a[j].y *= E;
-                }
-            }
-            if (isA) {
-                uint32_t h[4], l[4];
-                if (TF32) {
-#pragma unroll
-                    for (int j = 0; j < SPC; j++) {
-                        split_tf32(a[j].x, h[2 * j], l[2 * j]);
-                        split_tf32(a[j].y, h[2 * j + 1], l[2 * j + 1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < SPC; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
-                }
-                st16(stg + o_row, h[0], h[1], h[2], h[3]);
-                st16(stg + A_BYTES + o_row, l[0], l[1], l[2], l[3]);
-            } else {
-#pragma unroll
-                for (int x = 0; x < 2; x++) {   // B rows (q, X): X_s A_qs, and i X_s A_qs
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int j = 0; j < SPC; j++) {
-                        const float X = xp == 0 ? (x == 0 ? L.x[j].x : L.x[j].y) : (x == 0 ? L.x[j].z : L.x[j].w);
-                        if (TF32) {
-                            split_tf32(X * a[j].x, h[2 * j], l[2 * j]);
-                            split_tf32(X * a[j].y, h[2 * j + 1], l[2 * j + 1]);
-                        } else {
-                            split_bf16(X * a[j].x, X * a[j].y, h[j], l[j]);
-                        }
-                    }
-                    unsigned char *bh = stg + 2 * A_BYTES, *blo = bh + B_BYTES;
-                    st16(bh + o_row + 16 * x, h[0], h[1], h[2], h[3]);
-                    st16(blo + o_row + 16 * x, l[0], l[1], l[2], l[3]);
-                    if (TF32) {   // (re, im) -> (-im, re)
-                        st16(bh + o_im + 16 * x, h[1] ^ 0x80000000u, h[0], h[3] ^ 0x80000000u, h[2]);
-                        st16(blo + o_im + 16 * x, l[1] ^ 0x80000000u, l[0], l[3] ^ 0x80000000u, l[2]);
-                    } else {
-                        st16(bh + o_im + 16 * x, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
-                        st16(blo + o_im + 16 * x, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
-                    }
-                }
-            }
-        };
-        // one pipeline step: prefetch the next stage, wait for the slot
-        // (draining a finished segment meanwhile), form the operands
-        auto step = [&](int it, const Pre &use, Pre &next) -> bool {
-            if (it + 1 < nstg) load(it + 1, next);
-            const int slot = it % NST;
-            const uint32_t par = ((it / NST) & 1) ^ 1;
-            const uint64_t t0 = tc::global_ns();
-            for (uint32_t i = 0;; i++) {
-                // a completed phase stays complete until this slot is refilled,
-                // so the lanes agree once all have seen it
-                if (__all_sync(0xffffffffu, tc::mbar_try_wait_sleep(&empty[slot], par, isA ? 1000u : 20000u))) break;
-                if (isA && ready()) drain();
-                if ((i & 63) == 63 &&
-                    __any_sync(0xffffffffu, abort_flag != 0 || tc::global_ns() - t0 > 2000000000ull))
-                    return false;
-            }
-            produce(it, use);
-            tc::fence_async_smem();
-            tc::mbar_arrive(&full[slot]);
-            // a segment can only have finished once its last stage was formed
-            if (isA && it >= (nd + 1) * SEG && ready()) drain();
-            return true;
-        };
-        Pre b0, b1;
-        if (nstg > 0) load(0, b0);
-        bool ok = true;
-        for (int it = 0; it < nstg && ok; it += 2) {
-            ok = step(it, b0, b1);
-            if (ok && it + 1 < nstg) ok = step(it + 1, b1, b0);
-        }
-        if (isA) {
-            // the remaining segments
-            while (ok && nd < nseg) {
-                const bool got =
-                    __all_sync(0xffffffffu, tc::mbar_wait(&seg_full[nd & 1], (nd >> 1) & 1, &abort_flag));
-                if (!got) ok = false;
-                else drain();
-            }
-        }
-        if (!ok) abort_flag = 1;
-        ok = __all_sync(0xffffffffu, ok && abort_flag == 0);
-        if (!ok && lane == 0) atomicOr(&P.status->err[EC_RUN], EB_TIMEOUT);
-
-        // ------------------------------------------------------------ epilogue
-        // A warps: row p = lrow against q = 16 half .. 16 half + 15, from this
-        // thread's own running sums
-        if (ok && isA) {
-            const int pgl = p0 + lrow;
-            const bool prow = pgl < P.na;
-            float2 gp[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
-            if (P.has_gains && prow) {
-                const float4 *g4 =
-                    reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + pgl) * P.nchan + k));
-                const float4 a01 = g4[0], a23 = g4[1];
-                gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
-                gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
-            }
-            const long long rowbase = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 - pgl - 1;
-#pragma unroll 2
-            for (int i = 0; i < 16; i++) {
-                const int ql = 16 * half + i, q = q0 + ql;
-                if (!(prow && pgl < q && q < P.na)) continue;
-                float Sv[8];   // Re I, Q, U, V then Im I, Q, U, V
-#pragma unroll
-                for (int x = 0; x < 4; x++) {
-                    Sv[x] = nseg > 0 ? totals[(4 * ql + x) * 128 + lrow] : 0.f;
-                    Sv[4 + x] = nseg > 0 ? totals[(128 + 4 * ql + x) * 128 + lrow] : 0.f;
-                }
-                float2 Sm[4];
-                Sm[0] = make_float2(Sv[0] + Sv[1], Sv[4] + Sv[5]);   // I + Q
-                Sm[1] = make_float2(Sv[2] - Sv[7], Sv[6] + Sv[3]);   // U + iV
-                Sm[2] = make_float2(Sv[2] + Sv[7], Sv[6] - Sv[3]);   // U - iV
-                Sm[3] = make_float2(Sv[0] - Sv[1], Sv[4] - Sv[5]);   // I - Q
-                float2 gq[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
-                if (P.has_gains) {
-                    const float4 *g4 =
-                        reinterpret_cast<const float4 *>(P.gains + 4 * (((long long)t * P.na + q) * P.nchan + k));
-                    const float4 b01 = g4[0], b23 = g4[1];
-                    gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
-                    gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
-                }
-                float2 V[4], tmp[4], gqh[4];
-                mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
-                mherm(gq, gqh);
-                mmul(tmp, gqh, V);
-                const long long vrow = ((long long)t * P.nbl + rowbase + q) * P.nchan + k;
-                if (WRITE) {
-                    float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * vrow);
-                    o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
-                    o[1] = make_float4(V[2].x, V[2].y, V[3].x, V[3].y);
-                } else {
-                    const float4 *d4 = reinterpret_cast<const float4 *>(P.data + 4 * vrow);
-                    const float4 d01 = d4[0], d23 = d4[1];
-                    const float2 D[4] = {make_float2(d01.x, d01.y), make_float2(d01.z, d01.w),
-                                         make_float2(d23.x, d23.y), make_float2(d23.z, d23.w)};
-                    float r2 = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const float dr = V[c].x - D[c].x, di = V[c].y - D[c].y;
-                        r2 += dr * dr + di * di;
-                    }
-                    const float w = P.has_weight ? P.weight[vrow] : 1.f;
-                    chi += (double)(w * r2);
-                }
-            }
-        }
-    } else if (lane == 0) {
-        // ------------------------------------------------------------ MMA issuer
-        const uint32_t idesc = tc::instr_desc(TF32 ? tc::kFmtTF32 : tc::kFmtBF16, PT, NB);
-        const uint32_t sbase = tc::smem_u32(smem);
-        for (int it = 0; it < nstg; it++) {
-            const int g = it / SEG, b = g & 1, first = it % SEG == 0;
-            if (first && g >= 2 && !tc::mbar_wait(&seg_empty[b], ((g >> 1) - 1) & 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            const int slot = it % NST;
-            if (!tc::mbar_wait(&full[slot], (it / NST) & 1, &abort_flag)) {
-                abort_flag = 1;
-                break;
-            }
-            tc::tc_fence_after();
-            const uint32_t sb = sbase + slot * STAGE_BYTES;
-            const uint64_t ah = tc::smem_desc(sb), alo = tc::smem_desc(sb + A_BYTES);
-            const uint64_t bh = tc::smem_desc(sb + 2 * A_BYTES), bl = tc::smem_desc(sb + 2 * A_BYTES + B_BYTES);
-            const uint32_t d = tmem + 256 * b;   // columns: Re S (B rows 0-127), Im S (rows 128-255)
-            if (TF32) {
-                tc::mma_tf32(d, alo, bh, idesc, !first);
-                tc::mma_tf32(d, ah, bl, idesc, 1);
-                tc::mma_tf32(d, ah, bh, idesc, 1);
-            } else {
-                tc::mma_bf16(d, alo, bh, idesc, !first);
-                tc::mma_bf16(d, ah, bl, idesc, 1);
-                tc::mma_bf16(d, ah, bh, idesc, 1);
-            }
-            tc::mma_commit(&empty[slot]);
-            if (it % SEG == SEG - 1 || it == nstg - 1) tc::mma_commit(&seg_full[b]);
-        }
+    if (warp < NDRAIN / 32) {
+        tc::regs_inc<REGS_A>();
+        chi = role_a<TF32, WRITE>(C, tid, warp, lane);
+    } else if (warp < NPROD / 32) {
+        tc::regs_dec<REGS_B>();
+        role_b<TF32>(C, warp, lane);
+    } else {
+        tc::regs_dec<REGS_MMA>();
+        if (warp == NPROD / 32 && lane == 0) role_mma<TF32>(C);
     }
+    const uint32_t tmem = tmem_base;
 
     // ---------------------------------------------------------------- teardown
     tc::tc_fence_before();
@@ -615,7 +702,13 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
     P.result = result;
     P.status = c->d_status;
     auto go = [&](auto kernel) -> cudaError_t {
-        cudaError_t e2 = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        // the warpgroup register budgets assume the block is launched with
+        // exactly REGS_LAUNCH registers per thread; never launch otherwise
+        cudaFuncAttributes fa;
+        cudaError_t e2 = cudaFuncGetAttributes(&fa, kernel);
+        if (e2 != cudaSuccess) return e2;
+        if (fa.numRegs != REGS_LAUNCH) return cudaErrorInvalidConfiguration;
+        e2 = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
         if (e2 != cudaSuccess) return e2;
         kernel<<<(unsigned)blocks, THREADS, SMEM_BYTES, c->stream>>>(P);
         return cudaGetLastError();
