@@ -159,6 +159,46 @@ def _timed(torch, stream, fn, reps):
     return statistics.median(a.elapsed_time(b) for a, b in ev)
 
 
+def form_small_latency(torch, R):
+    """The 7-antenna, 10-timestep, 16-channel, 10-point FP64 workload (3360
+    visibilities): latency-bound, so the time of one chi^2 replayed from a
+    CUDA graph (result left on the device) is the number that matters."""
+    wl = rime_synth.WORKLOADS["7ant-10t-16ch-10pt"]
+    inp = rime_synth.make_inputs(wl, precision="f64")
+    stream = torch.cuda.Stream()
+    ctx = R.Rime(inp, R.RIME_FP64, weight=inp["weight"], stream=stream)
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])
+    V = ctx.predict()
+    ctx.set_data(V.cpu().numpy() + inp["noise"], inp["weight"])
+    del V
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.chi2_async(out)
+    ctx.sync()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        g.capture_begin(capture_error_mode="relaxed")
+        for _ in range(100):
+            ctx.chi2_async(out)
+        g.capture_end()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):   # replays run on the current stream
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            g.replay()
+        e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / 1000
+    eager = _timed(torch, stream, lambda: ctx.chi2_async(out), 50) * 1e3
+    ctx.close()
+    return {"workload": wl.name, "dtype": "f64", "us_per_chi2_graph": us,
+            "us_per_chi2_eager_call": eager, "eager_note": "one rime_chi2_async call per chi^2 from Python; "
+            "the gap between calls is host time",
+            "chi2_evals_per_s": 1e6 / us}
+
+
 def form_grad(torch, R, chi2_ms):
     """Adjoint gradient (rime_chi2_grad) on the 64-antenna gradient workload,
     against the plain fused chi^2 of the same workload."""
@@ -525,7 +565,8 @@ def main():
         line["roofline"]["frac_at_median_clock"] = achieved / peak_fp32_tflops(clocks["sm_mhz"])
     ctx.close()
     if rank == 0 and world == 1 and not args.no_forms and args.precision == "f32":
-        line["forms"] = {"gradient": form_grad(torch, R, ms_per_step),
+        line["forms"] = {"small_fp64_latency": form_small_latency(torch, R),
+                         "gradient": form_grad(torch, R, ms_per_step),
                          "batched": form_batched(torch, R),
                          "split_precision": form_split(torch, R)}
     if rank == 0 and not args.no_cpu_baseline:

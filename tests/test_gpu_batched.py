@@ -179,6 +179,27 @@ def test_batched_full_size_sampled_sets():
         assert rel_err(got[j], want) <= TOL["f32"]["chi2"], (j, got[j], want)
 
 
+def test_batched_512_sets_against_oracle_on_a_slice():
+    """All 512 sets of the batched workload (5..500 sources) on its first 4
+    timesteps: the smallest, the largest and 6 seeded sets against the FP64
+    oracle (chi^2 tolerance of the FP32 path)."""
+    inp = rime_synth.make_inputs("64ant-50t-32ch-512sets", precision="f32")
+    nt = 4
+    sl = dict(inp, ntime=nt, uvw=inp["uvw"][:nt], gains=inp["gains"][:nt], weight=inp["weight"][:nt],
+              noise=inp["noise"][:nt])
+    sl["data"] = rime_synth.observe(oracle.Problem(sl).predict(), sl["noise"], "f32")
+    sets = inp["sets"]
+    r = gpu_ctx(sl, "f32")
+    got = _run(r, sets)
+    r.close()
+    counts = np.diff(sets["offsets"])
+    rng = np.random.default_rng(11)
+    pick = {int(np.argmin(counts)), int(np.argmax(counts))} | {int(j) for j in rng.choice(512, 6, replace=False)}
+    for j in sorted(pick):
+        want = oracle.Problem(sl, sources=set_sources(sets, j), data=sl["data"]).chi2()
+        assert rel_err(got[j], want) <= TOL["f32"]["chi2"], (j, counts[j], got[j], want)
+
+
 def test_batched_argument_errors():
     import paper_1501_07719_gb300 as R
     inp = _case("13ant", "f64")

@@ -122,6 +122,31 @@ def test_split_rejects_gaussian_sources_and_fp64():
     r.close()
 
 
+def test_split_256ant_slice_chi2_against_oracle():
+    """The 256-antenna, 4096-point workload on one timestep and two channels
+    (267 M source-terms): chi^2 of both splits and of the direct path against
+    the FP64 oracle; data = model + noise, so V - D is at the noise level."""
+    import paper_1501_07719_gb300 as R
+    inp = rime_synth.make_inputs("256ant-20t-128ch-4096pt", precision="f32")
+    sl = dict(inp, ntime=1, nchan=2, freq=inp["freq"][:2], uvw=inp["uvw"][:1], gains=inp["gains"][:1, :, :2],
+              weight=inp["weight"][:1, :, :2], noise=inp["noise"][:1, :, :2])
+    P = oracle.Problem(sl)
+    sl["data"] = rime_synth.observe(P.predict(), sl["noise"], "f32")
+    want = oracle.Problem(sl, data=sl["data"]).chi2()
+    r = gpu_ctx(sl, "f32")
+    # 4096 sources make |V| ~ 1e2 Jy against 0.01 Jy of noise. The direct FP32
+    # sum rounds each of its 4096 additions at 2^-24 |V| (~1e-5 Jy), ~5e-4 Jy
+    # in all, which shows in chi^2 at ~1e-4 (measured 1.2e-4); the TF32 split
+    # adds short MMA segments into its running sums and does better. The BF16
+    # split's |dV| (~4e-6 of max |V|) shows at ~1e-3.
+    for mode, tol in ((R.RIME_TC_OFF, 2e-4), (R.RIME_TC_SPLIT_BF16, 2e-3),
+                      (R.RIME_TC_SPLIT_TF32, CTOL["tf32"])):
+        r.set_tensor_mode(mode)
+        got = r.chi2()
+        assert rel_err(got, want) <= tol, (mode, got, want)
+    r.close()
+
+
 @pytest.mark.parametrize("split", ["bf16", "tf32"])
 def test_split_full_256ant_sampled(split):
     """The 256-antenna, 20-timestep, 128-channel, 4096-point workload in the
