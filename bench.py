@@ -449,6 +449,7 @@ def main():
 
     import torch
     import paper_1501_07719_gb300 as R
+    from paper_1501_07719_gb300 import shard
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -499,9 +500,7 @@ def main():
     total_ms = e_start.elapsed_time(e_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = shard.reduce_max(total_ms)   # the slowest rank
     ms_per_step = total_ms / args.steps
     terms = terms_of(wl)
     value = terms * world / (ms_per_step * 1e-3)
@@ -527,9 +526,7 @@ def main():
             e2e_times.append(dt)
     e2e_s = statistics.median(e2e_times)
     if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = shard.reduce_max(e2e_s)
     assert chi_e2e == chi_check, (chi_e2e, chi_check)
 
     peaks = measured_peaks()
