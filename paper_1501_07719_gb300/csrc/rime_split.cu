@@ -71,6 +71,9 @@ constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr uint32_t SMEM_BYTES = NST * STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 512;     // two buffers of (Re, Im) x 128 columns
 static_assert(SMEM_BYTES + 1024 <= 227 * 1024, "shared memory");
+// the epilogue stores the running sums ([256 columns][128 rows] of float)
+// in the stage buffers, so they must hold them
+static_assert(SMEM_BYTES >= 256u * 128u * 4u, "stage buffers smaller than the epilogue's sums");
 static_assert(STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 && B_BYTES % 16 == 0, "operand alignment");
 
 struct SplitParams {
@@ -117,9 +120,18 @@ __device__ __forceinline__ uint32_t pack_bf16(float x, float y) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(y), "f"(x));
     return r;
 }
+// x = hi + lo with hi = x rounded to 8 significant bits by Veltkamp's
+// splitting (c = 2^16 + 1; each step rounded separately, no FMA contraction,
+// so hi converts to BF16 without rounding) and lo = x - hi exactly, then
+// rounded to BF16.
+__device__ __forceinline__ float veltkamp_hi8(float x) {
+    const float t = __fmul_rn(x, 65537.0f);
+    return __fsub_rn(t, __fsub_rn(t, x));
+}
 __device__ __forceinline__ void split_bf16(float x, float y, uint32_t &hi, uint32_t &lo) {
-    hi = pack_bf16(x, y);
-    lo = pack_bf16(x - __uint_as_float(hi << 16), y - __uint_as_float(hi & 0xffff0000u));
+    const float xh = veltkamp_hi8(x), yh = veltkamp_hi8(y);
+    hi = pack_bf16(xh, yh);
+    lo = pack_bf16(__fsub_rn(x, xh), __fsub_rn(y, yh));
 }
 // (x, y) word -> (-y, x): the same pair multiplied by i
 __device__ __forceinline__ uint32_t rot_bf16(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x00008000u; }
@@ -200,10 +212,18 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
     const int lrow = 32 * quad + lane;
     const ChanF ch = C.ch;
 
+    const float2 *tau0 = P.tau + tbase;
+    const int na = P.na, last = P.nsrc - 1;
     auto load = [&](int it, Pre<SPC> &L) {
         const int sb = it * SPS + chunk * SPC;
+        if (sb + SPC - 1 <= last) {   // all sources live (warp-uniform)
+            const float2 *p = tau0 + (size_t)sb * na;
 #pragma unroll
-        for (int j = 0; j < SPC; j++) L.tau[j] = P.tau[tbase + (long long)min(sb + j, P.nsrc - 1) * P.na];
+            for (int j = 0; j < SPC; j++) L.tau[j] = p[j * na];
+        } else {
+#pragma unroll
+            for (int j = 0; j < SPC; j++) L.tau[j] = tau0[(size_t)min(sb + j, last) * na];
+        }
     };
     // FP32 running sums of this thread's accumulator columns: Re S then Im S
     // for columns 64 half .. 64 half + 63 of each
@@ -380,13 +400,21 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
     const bool pointing = P.has_pointing != 0;
     const ChanF ch = C.ch;
 
+    const float2 *tau0 = P.tau + tbase;
+    const int na = P.na, last = P.nsrc - 1;
     auto load = [&](int it, Pre<SPC> &L) {
         const int sb = it * SPS + chunk * SPC;
+        const float2 *xs = scale + 2 * sb + xp;   // zero past the last source
+        if (sb + SPC - 1 <= last) {
+            const float2 *p = tau0 + (size_t)sb * na;
 #pragma unroll
-        for (int j = 0; j < SPC; j++) {
-            L.tau[j] = P.tau[tbase + (long long)min(sb + j, P.nsrc - 1) * P.na];
-            L.x[j] = scale[2 * (sb + j) + xp];   // zero past the last source
+            for (int j = 0; j < SPC; j++) L.tau[j] = p[j * na];
+        } else {
+#pragma unroll
+            for (int j = 0; j < SPC; j++) L.tau[j] = tau0[(size_t)min(sb + j, last) * na];
         }
+#pragma unroll
+        for (int j = 0; j < SPC; j++) L.x[j] = xs[2 * j];
     };
     auto produce = [&](int it, const Pre<SPC> &L) {
         unsigned char *bh = C.smem + (it % NST) * STAGE_BYTES + 2 * A_BYTES, *blo = bh + B_BYTES;
