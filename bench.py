@@ -285,7 +285,7 @@ def form_batched(torch, R):
             "tflops": flops / (batched_ms * 1e-3) / 1e12, "first_call_s_incl_tuning": first_s,
             "max_rel_diff_vs_plain": float(rel.max()),
             "launch": "captured CUDA graph: schedule upload, source prep, one persistent kernel, per-set sums",
-            "tuned": {k: cfg[k] for k in ("channels_per_item", "blocks_per_sm", "order", "tuned")},
+            "tuned": {k: cfg[k] for k in ("channels_per_item", "blocks_per_sm", "order", "sets_per_item", "tuned")},
             "trials_ms": [round(t["ms"], 3) for t in cfg["trials"]]}
 
 

@@ -196,17 +196,19 @@ typedef enum {
 rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 
 /* Configuration of the batched FP32 launch, and the autotuner's record.
- * A work item of the persistent launch is (set, timestep, group of
- * channels_per_item channels, antenna unit), each covering all of the set's
- * sources; the grid holds blocks_per_sm blocks per SM. */
+ * A work item of the persistent launch is (timestep, group of
+ * channels_per_item channels, antenna unit, group of sets_per_item sets),
+ * each set with all of its sources; the grid holds blocks_per_sm blocks per
+ * SM. Sets of one item share their data, weights and gains. */
 typedef struct {
     int32_t channels_per_item;  /* 1, 2 or 4 */
     int32_t blocks_per_sm;      /* 1 or 2 */
     int32_t order;              /* 0: largest sets first, 1: in set order */
+    int32_t sets_per_item;      /* 1 .. 64 (the tuner tries 1, 4, 16) */
     int32_t tuned;              /* out: 1 if chosen by timing trials */
-    int32_t ntrials;            /* out: configurations timed, <= 16 */
-    int32_t trial_cfg[16][3];   /* out: (channels_per_item, blocks_per_sm, order) of each trial */
-    float trial_ms[16];         /* out: its time on the trial sample, ms */
+    int32_t ntrials;            /* out: configurations timed, <= 40 */
+    int32_t trial_cfg[40][4];   /* out: (channels_per_item, blocks_per_sm, order, sets_per_item) */
+    float trial_ms[40];         /* out: each trial's time on the trial sample, ms */
 } rime_batch_config;
 
 /* chi^2 (eq. 7) of nsets sky models against the context's observation, data
@@ -236,7 +238,7 @@ rime_status rime_chi2_batched(rime_ctx *ctx, int32_t nsets, const int32_t *src_o
  * the first call). */
 rime_status rime_batched_config(const rime_ctx *ctx, rime_batch_config *out);
 
-/* Fixes the configuration of later batched calls (its first three fields;
+/* Fixes the configuration of later batched calls (its first four fields;
  * the rest is ignored); NULL returns to timing trials. */
 rime_status rime_set_batched_config(rime_ctx *ctx, const rime_batch_config *cfg);
 

@@ -31,8 +31,8 @@ class rime_sources(C.Structure):
 
 class rime_batch_config(C.Structure):
     _fields_ = [("channels_per_item", C.c_int32), ("blocks_per_sm", C.c_int32), ("order", C.c_int32),
-                ("tuned", C.c_int32), ("ntrials", C.c_int32), ("trial_cfg", (C.c_int32 * 3) * 16),
-                ("trial_ms", C.c_float * 16)]
+                ("sets_per_item", C.c_int32), ("tuned", C.c_int32), ("ntrials", C.c_int32),
+                ("trial_cfg", (C.c_int32 * 4) * 40), ("trial_ms", C.c_float * 40)]
 
 
 class RimeError(RuntimeError):
@@ -271,17 +271,18 @@ def rime_batched_config(ctx) -> dict:
     c = rime_batch_config()
     _check(lib().rime_batched_config(ctx, C.byref(c)), ctx)
     trials = [dict(channels_per_item=c.trial_cfg[i][0], blocks_per_sm=c.trial_cfg[i][1],
-                   order=c.trial_cfg[i][2], ms=float(c.trial_ms[i])) for i in range(c.ntrials)]
+                   order=c.trial_cfg[i][2], sets_per_item=c.trial_cfg[i][3], ms=float(c.trial_ms[i]))
+              for i in range(c.ntrials)]
     return dict(channels_per_item=c.channels_per_item, blocks_per_sm=c.blocks_per_sm, order=c.order,
-                tuned=bool(c.tuned), trials=trials)
+                sets_per_item=c.sets_per_item, tuned=bool(c.tuned), trials=trials)
 
 
-def rime_set_batched_config(ctx, channels_per_item=None, blocks_per_sm=2, order=0):
+def rime_set_batched_config(ctx, channels_per_item=None, blocks_per_sm=2, order=0, sets_per_item=1):
     """Fixes the batched configuration; channels_per_item=None returns to tuning."""
     if channels_per_item is None:
         _check(lib().rime_set_batched_config(ctx, None), ctx)
         return
-    c = rime_batch_config(channels_per_item, blocks_per_sm, order)
+    c = rime_batch_config(channels_per_item, blocks_per_sm, order, sets_per_item)
     _check(lib().rime_set_batched_config(ctx, C.byref(c)), ctx)
 
 

@@ -90,8 +90,8 @@ class Rime:
     def batched_config(self) -> dict:
         return A.rime_batched_config(self.ctx)
 
-    def set_batched_config(self, channels_per_item=None, blocks_per_sm=2, order=0):
-        A.rime_set_batched_config(self.ctx, channels_per_item, blocks_per_sm, order)
+    def set_batched_config(self, channels_per_item=None, blocks_per_sm=2, order=0, sets_per_item=1):
+        A.rime_set_batched_config(self.ctx, channels_per_item, blocks_per_sm, order, sets_per_item)
 
     def ln_norm(self) -> float:
         return A.rime_ln_norm(self.ctx)

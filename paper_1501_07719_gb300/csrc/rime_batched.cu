@@ -2,15 +2,17 @@
 // proposals of one sampler iteration) against one observation.
 //
 // FP32: one persistent launch (k_batched_f32, rime_fused.cu) over work items
-// (set, t, channel group, antenna unit), each the fused predict + chi^2 of one
-// set's sources for the unit's baselines, then one fixed-order sum per set.
+// (t, channel group, antenna unit, group of sets), each the fused predict +
+// chi^2 of its sets' sources for the unit's baselines, then one fixed-order
+// sum per set.
 // FP64: one launch of the FP64 fused kernel per set.
 //
 // The schedule (set order and source offsets) reaches the device as kernel
 // arguments, so a captured CUDA graph carries it and replays stand alone.
-// The launch configuration is chosen by timing each candidate on a sample of
-// the work (the first timesteps of every set) on the first call for a given
-// number of sets and sources, unless a call fixes it.
+// The launch configuration (channels and sets per work item, blocks per SM,
+// set order) is chosen by timing each candidate on a sample of the work (the
+// first timesteps of every set) on the first call for a given number of sets
+// and sources, unless a call fixes it.
 #include "rime_internal.cuh"
 
 #include <algorithm>
@@ -53,6 +55,7 @@ cudaError_t put_ints(int *dst, const int *src, size_t n, cudaStream_t st) {
 }
 
 constexpr int kCpi[] = {1, 2, 4};
+constexpr int kGsets[] = {1, 4, 16};
 
 struct Sched {
     int nsets;
@@ -65,8 +68,10 @@ BatchParams batch_params(rime_ctx *c, const Sched &S, const rime_batch_config &c
     BatchParams B{};
     B.cpi = cfg.channels_per_item;
     B.nkc = (c->dims.nchan + B.cpi - 1) / B.cpi;
-    B.items_per_set = ntime_items * B.nkc * c->nunits;
-    B.nitems = (long long)S.nsets * B.items_per_set;
+    B.nsets = S.nsets;
+    B.gsets = cfg.sets_per_item;
+    B.ngroups = (S.nsets + B.gsets - 1) / B.gsets;
+    B.nitems = (long long)ntime_items * B.nkc * c->nunits * B.ngroups;
     B.per_set = S.per_set;
     B.order = S.order[cfg.order];
     B.offsets = S.offsets;
@@ -89,14 +94,18 @@ rime_status tune(rime_ctx *c, const Sched &S, rime_batch_config &best) {
     std::vector<rime_batch_config> cand;
     for (int cpi : kCpi) {
         if (cpi > 1 && cpi > c->dims.nchan) continue;
-        for (int bps = std::min(2, c->bmax_bps); bps >= 1; bps--)
-            for (int order = 0; order < 2; order++) {
-                rime_batch_config x{};
-                x.channels_per_item = cpi;
-                x.blocks_per_sm = bps;
-                x.order = order;
-                cand.push_back(x);
-            }
+        for (int gs : kGsets) {
+            if (gs > 1 && gs > S.nsets) continue;
+            for (int bps = std::min(2, c->bmax_bps); bps >= 1; bps--)
+                for (int order = 0; order < 2; order++) {
+                    rime_batch_config x{};
+                    x.channels_per_item = cpi;
+                    x.blocks_per_sm = bps;
+                    x.order = order;
+                    x.sets_per_item = gs;
+                    cand.push_back(x);
+                }
+        }
     }
     cudaEvent_t e0, e1;
     CKB(c, cudaEventCreate(&e0), "tuning events");
@@ -105,7 +114,7 @@ rime_status tune(rime_ctx *c, const Sched &S, rime_batch_config &best) {
     int ibest = -1;
     float tbest = 0.f;
     cudaError_t err = cudaSuccess;
-    for (size_t i = 0; i < cand.size() && err == cudaSuccess && i < 16; i++) {
+    for (size_t i = 0; i < cand.size() && err == cudaSuccess && i < 40; i++) {
         float tmin = 0.f;
         for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
             err = cudaEventRecord(e0, c->stream);
@@ -119,6 +128,7 @@ rime_status tune(rime_ctx *c, const Sched &S, rime_batch_config &best) {
         rec.trial_cfg[i][0] = cand[i].channels_per_item;
         rec.trial_cfg[i][1] = cand[i].blocks_per_sm;
         rec.trial_cfg[i][2] = cand[i].order;
+        rec.trial_cfg[i][3] = cand[i].sets_per_item;
         rec.trial_ms[i] = tmin;
         rec.ntrials = (int)i + 1;
         if (ibest < 0 || tmin < tbest) {
@@ -132,6 +142,7 @@ rime_status tune(rime_ctx *c, const Sched &S, rime_batch_config &best) {
     rec.channels_per_item = cand[ibest].channels_per_item;
     rec.blocks_per_sm = cand[ibest].blocks_per_sm;
     rec.order = cand[ibest].order;
+    rec.sets_per_item = cand[ibest].sets_per_item;
     rec.tuned = 1;
     best = rec;
     return RIME_OK;
@@ -225,6 +236,7 @@ rime_status rime_chi2_batched(rime_ctx *c, int32_t nsets, const int32_t *off, co
                 cfg.channels_per_item = 1;
                 cfg.blocks_per_sm = std::min(2, c->bmax_bps);
                 cfg.order = 0;
+                cfg.sets_per_item = 1;
             }
         }
     }
@@ -252,10 +264,13 @@ rime_status rime_set_batched_config(rime_ctx *c, const rime_batch_config *cfg) {
     if (cfg->blocks_per_sm != 1 && cfg->blocks_per_sm != 2)
         return fail_ctx(c, RIME_E_INVALID, "blocks_per_sm must be 1 or 2");
     if (cfg->order != 0 && cfg->order != 1) return fail_ctx(c, RIME_E_INVALID, "order must be 0 or 1");
+    if (cfg->sets_per_item < 1 || cfg->sets_per_item > 64)
+        return fail_ctx(c, RIME_E_INVALID, "sets_per_item must be 1..64");
     rime_batch_config x{};
     x.channels_per_item = cpi;
     x.blocks_per_sm = cfg->blocks_per_sm;
     x.order = cfg->order;
+    x.sets_per_item = cfg->sets_per_item;
     c->bcfg = x;
     c->bcfg_forced = true;
     return RIME_OK;

@@ -803,10 +803,12 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
 }
 
 // Batched chi^2: many source sets against one observation in one persistent
-// launch. A work item is (set rank, t, channel group, unit); blocks take
-// items from a counter (ranks in the order given, largest sets first by
-// default) and store one partial per (set, t, channel, unit), so the sums do
-// not depend on the schedule.
+// launch. A work item is (t, channel group, unit, group of sets); blocks take
+// items from a counter. Items run in (t, channel group, unit) order and,
+// within it, sets by rank (largest first by default), so the sets of one
+// item share their data, weights and gains, which the later sets read from
+// L1. One partial per (set, t, channel, unit): the sums do not depend on the
+// schedule.
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(const FusedParams P, const BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -818,19 +820,22 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(co
         __syncthreads();
         const long long item = sItem;
         if (item >= B.nitems) break;
-        const int rank = (int)(item / B.items_per_set);
-        const int w = (int)(item - (long long)rank * B.items_per_set);
-        const int j = B.order[rank];
+        const int w = (int)(item / B.ngroups);
+        const int g = (int)(item - (long long)w * B.ngroups);
         const int u = w % P.nunits;
         const int rest = w / P.nunits;
         const int kc = rest % B.nkc;
         const int t = rest / B.nkc;
         const int k1 = min(P.nchan, (kc + 1) * B.cpi);
-        for (int k = kc * B.cpi; k < k1; k++) {
-            const double bsum = fused_item<MODE_CHI2>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
-            if (threadIdx.x == 0)
-                B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
-            __syncthreads();
+        const int r1 = min(B.nsets, (g + 1) * B.gsets);
+        for (int rank = g * B.gsets; rank < r1; rank++) {
+            const int j = B.order[rank];
+            for (int k = kc * B.cpi; k < k1; k++) {
+                const double bsum = fused_item<MODE_CHI2>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
+                if (threadIdx.x == 0)
+                    B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
+                __syncthreads();
+            }
         }
     }
 }

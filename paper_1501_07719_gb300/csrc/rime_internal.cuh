@@ -118,10 +118,10 @@ struct FusedParams {
 };
 
 // Batched chi^2: the schedule of a persistent launch. Work item i is
-// (rank, t, channel group, unit) with rank = i / items_per_set.
+// (t, channel group, unit) = i / ngroups and the group of sets i % ngroups.
 struct BatchParams {
-    long long nitems;          // ranks * items_per_set (fewer ranks or timesteps in a tuning trial)
-    int items_per_set;         // timesteps covered * nkc * nunits
+    long long nitems;          // (timesteps covered * nkc * nunits) * ngroups
+    int nsets, gsets, ngroups; // sets; sets per item; ceil(nsets / gsets)
     int per_set;               // partials per set: ntime * nchan * nunits
     int nkc, cpi;              // channel groups, channels per group
     const int *order;          // set of each rank

@@ -96,12 +96,13 @@ def test_batched_configurations_agree_bitwise():
     for cpi in (1, 2, 4):
         for bps in (1, 2):
             for order in (0, 1):
-                r.set_batched_config(cpi, bps, order)
-                got = _run(r, sets)
-                cfg = r.batched_config()
-                assert (cfg["channels_per_item"], cfg["order"]) == (cpi, order)
-                assert not cfg["tuned"]
-                np.testing.assert_array_equal(got, ref)
+                for gs in (1, 3, 64):
+                    r.set_batched_config(cpi, bps, order, gs)
+                    got = _run(r, sets)
+                    cfg = r.batched_config()
+                    assert (cfg["channels_per_item"], cfg["order"], cfg["sets_per_item"]) == (cpi, order, gs)
+                    assert not cfg["tuned"]
+                    np.testing.assert_array_equal(got, ref)
     r.close()
 
 
@@ -113,8 +114,8 @@ def test_tuner_picks_its_fastest_trial():
     r.close()
     assert cfg["tuned"] and len(cfg["trials"]) >= 4
     best = min(cfg["trials"], key=lambda x: x["ms"])
-    assert (cfg["channels_per_item"], cfg["blocks_per_sm"], cfg["order"]) == \
-        (best["channels_per_item"], best["blocks_per_sm"], best["order"])
+    assert (cfg["channels_per_item"], cfg["blocks_per_sm"], cfg["order"], cfg["sets_per_item"]) == \
+        (best["channels_per_item"], best["blocks_per_sm"], best["order"], best["sets_per_item"])
     assert all(t["ms"] > 0 for t in cfg["trials"])
 
 
@@ -221,6 +222,8 @@ def test_batched_argument_errors():
     assert out.numel() == 0
     with pytest.raises(R.RimeError):
         r.set_batched_config(3, 2, 0)
+    with pytest.raises(R.RimeError):
+        r.set_batched_config(1, 2, 0, 0)
     r.close()
 
 
