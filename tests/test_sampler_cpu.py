@@ -1,0 +1,54 @@
+"""The ensemble Metropolis driver's host logic with stand-in scorers (no
+GPU): acceptance rule, bounds, determinism, and that chains sample a known
+Gaussian posterior."""
+import numpy as np
+import pytest
+
+from paper_1501_07719_gb300 import sampler
+
+
+def _sky(n=3):
+    return dict(lm=np.zeros((n, 2)), stokes=np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)), alpha=np.full(n, -0.7),
+                shape=np.zeros((n, 3)))
+
+
+def test_log_likelihood_is_eq7():
+    assert sampler.log_likelihood(10.0, 4.0) == -7.0
+
+
+def test_flat_scorer_accepts_every_proposal_in_bounds():
+    s = sampler.EnsembleMetropolis(None, _sky(), 5, {"I": 0.5}, seed=3, bounds={"I": (0.0, 1.2)},
+                                   chi2_fn=lambda models: np.zeros(len(models)))
+    for _ in range(20):
+        acc = s.step()
+        assert np.all(s.theta["I"] >= 0.0) and np.all(s.theta["I"] <= 1.2)
+    # proposals outside the bounds were rejected, inside ones accepted
+    assert 0 < s.naccept.sum() < 5 * 20
+
+
+def test_chains_are_deterministic_under_a_seed():
+    f = lambda models: np.array([np.sum((m["lm"][:, 0] - 1e-3) ** 2) / 1e-8 for m in models])
+    runs = []
+    for _ in range(2):
+        s = sampler.EnsembleMetropolis(None, _sky(), 4, {"l": 1e-4}, seed=11, chi2_fn=f)
+        runs.append(s.run(30))
+    np.testing.assert_array_equal(runs[0]["accept"], runs[1]["accept"])
+    np.testing.assert_array_equal(runs[0]["chi2"], runs[1]["chi2"])
+
+
+def test_chains_sample_a_gaussian_posterior():
+    # chi^2 = ((l - mu) / sigma)^2 for each source: the posterior of l is N(mu, sigma^2)
+    mu, sigma = 2e-3, 5e-4
+    f = lambda models: np.array([np.sum(((m["lm"][:, 0] - mu) / sigma) ** 2) for m in models])
+    s = sampler.EnsembleMetropolis(None, _sky(2), 64, {"l": 1.5 * sigma}, seed=5, chi2_fn=f)
+    s.run(400)                                 # burn-in
+    out = s.run(2000, thin=10)
+    l = out["samples"]["l"].ravel()
+    assert abs(l.mean() - mu) < 0.05 * sigma * 10 and abs(l.std() - sigma) < 0.1 * sigma
+    rate = out["accept"].mean()
+    assert 0.2 < rate < 0.7
+
+
+def test_unknown_parameter_is_rejected():
+    with pytest.raises(ValueError):
+        sampler.EnsembleMetropolis(None, _sky(), 2, {"flux": 1.0}, seed=0, chi2_fn=lambda m: np.zeros(len(m)))
