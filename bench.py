@@ -397,14 +397,15 @@ def run_only(args):
     import paper_1501_07719_gb300 as R
     over = {k: v for k, v in (("ntime", args.ntime), ("nchan", args.nchan)) if v}
     wl = rime_synth.workload(args.workload, **over)
-    inp = rime_synth.make_inputs(wl, precision="f32")
-    w = inp["weight"].astype(np.float32)
+    f64 = args.precision == "f64"
+    inp = rime_synth.make_inputs(wl, precision=args.precision)
+    w = inp["weight"].astype(np.float64 if f64 else np.float32)
     stream = torch.cuda.current_stream()
-    ctx = R.Rime(inp, R.RIME_FP32, weight=w, stream=stream)
+    ctx = R.Rime(inp, R.RIME_FP64 if f64 else R.RIME_FP32, weight=w, stream=stream)
     ctx.set_gains(inp["gains"])
     ctx.set_sources(inp["sources"])
     V = ctx.predict()
-    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64), w)
+    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex128 if f64 else np.complex64), w)
     del V
     out = torch.zeros(max(1, wl.nsets), dtype=torch.float64, device="cuda")
     if args.only in ("chi2", "split-bf16", "split-tf32"):
