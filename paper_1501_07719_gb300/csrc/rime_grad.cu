@@ -152,7 +152,10 @@ struct GSmem {
         if (pointing) b += (size_t)GNLOC * SG * sizeof(T2);            // dlnE/dl, dlnE/dm
         b += (size_t)NBMAX * 4 * sizeof(T);                            // baseline table
         b += (size_t)2 * BLC * 4 * sizeof(T2);                         // Y chunks (double buffer)
-        return std::max(b, (size_t)GTHREADS * NGRAD * sizeof(double));
+        // the final combine: one FP64 row of NGRAD per (baseline group, source);
+        // a thread of the FP32 kernel holds two sources
+        const size_t red = (size_t)(sizeof(T) == 4 ? 2 : 1) * GTHREADS * NGRAD * sizeof(double);
+        return std::max(b, red);
     }
 };
 
@@ -380,6 +383,255 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     }
 }
 
+// FP32 version with two sources per thread: thread (source pair sp, baseline
+// group grp of 16); the pair's z, Gaussian factors and moments are computed
+// on packed FP32 pairs (one instruction for both sources), the baseline data
+// and Y_X are shared by the pair. Same staging, moments and channel factors as
+// k_grad_src.
+__device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 pdup(float a) { return make_float2(a, a); }
+
+__global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams P) {
+    using T = float;
+    using T2 = float2;
+    constexpr int SG = GCfg<float>::SG, NP = SG / 2, NG = GTHREADS / NP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *rTau = reinterpret_cast<float2 *>(smem_raw);
+    T *rRho = reinterpret_cast<T *>(rTau + SG * GNLOC);
+    T2 *sA = reinterpret_cast<T2 *>(rRho + SG * GNLOC);
+    T2 *sE = sA + GNLOC * SG;
+    T *sB = reinterpret_cast<T *>(P.has_pointing ? sE + GNLOC * SG : sE);
+    T2 *sY = reinterpret_cast<T2 *>(sB + 4 * NBMAX);
+    double *sRed = reinterpret_cast<double *>(smem_raw);   // reused at the end
+
+    if (inputs_bad(P.status)) return;
+    const int tid = threadIdx.x;
+    const int sp = tid % NP, grp = tid / NP;
+    int bid = blockIdx.x;
+    const int sch = bid % P.nsch;
+    bid /= P.nsch;
+    const int u = bid % P.nunits;
+    bid /= P.nunits;
+    const int cg = bid % P.ncg;
+    const int t = bid / P.ncg;
+    const Unit U = P.units[u];
+    const int nb = U.nbody;
+    const int nloc = U.diag ? U.nr : U.nr + U.nc;
+    const bool pointing = P.has_pointing != 0;
+    const int k0 = cg * P.chan_group, k1 = min(P.nchan, k0 + P.chan_group);
+
+    for (int i = tid; i < nloc * SG; i += GTHREADS) {
+        const int a = i / SG, ss = i - a * SG;
+        const int src = min(sch * SG + ss, P.nsrc - 1);
+        const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+        const long long di = ((long long)t * P.nsrc + src) * P.na + ant;
+        rTau[i] = reinterpret_cast<const float2 *>(P.tau)[di];
+        rRho[i] = reinterpret_cast<const T *>(P.rho)[di];
+    }
+    const uint16_t *bls = P.bls + U.tile0;
+    for (int i = tid; i < nb; i += GTHREADS) {
+        const uint16_t e = bls[i];
+        const int pl = e & 0xff, ql = e >> 8;
+        const int p = U.r0 + pl, q = U.c0 + ql;
+        const double *xp = P.uvw + 3 * ((long long)t * P.na + p);
+        const double *xq = P.uvw + 3 * ((long long)t * P.na + q);
+        const int la = pl, lb = U.diag ? ql : U.nr + ql;
+        T *b = sB + 4 * i;
+        b[0] = (T)(xp[0] - xq[0]);
+        b[1] = (T)(xp[1] - xq[1]);
+        b[2] = (T)(xp[2] - xq[2]);
+        b[3] = int_bits<T>((la * SG) | ((lb * SG) << 16));
+    }
+
+    // ---- per-source constants of this thread's two sources (the rest is read
+    // from the L1-resident tables once per channel, outside the baseline loop)
+    int sidx[2];
+    bool sact[2], is_gauss[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int s = sch * SG + 2 * sp + h;
+        sact[h] = s < P.nsrc;
+        sidx[h] = sact[h] ? s : P.nsrc - 1;
+        is_gauss[h] = reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] != T(0);
+    }
+    const bool any_gauss = is_gauss[0] || is_gauss[1];
+    const float4 st0 = reinterpret_cast<const float4 *>(P.stokes)[sidx[0]];
+    const float4 st1 = reinterpret_cast<const float4 *>(P.stokes)[sidx[1]];
+    const float2 sI = pf2(st0.x, st1.x), sQ = pf2(st0.y, st1.y);
+    const float2 sU = pf2(st0.z, st1.z), sV = pf2(st0.w, st1.w);
+    const double *ptab = pointing ? P.pointing + 2 * (long long)t * P.na : nullptr;
+    const T2 *yin = reinterpret_cast<const T2 *>(P.yin);
+
+    double out[2][NGRAD];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int i = 0; i < NGRAD; i++) out[h][i] = 0.0;
+
+    const int nchunk = (nb + BLC - 1) / BLC;
+    auto issue_y = [&](int j) {
+        const int kk = k0 + j / nchunk, b0 = (j % nchunk) * BLC;
+        const int cnt = min(BLC, nb - b0);
+        T2 *dst = sY + (j & 1) * BLC * 4;
+        for (int i = tid; i < 2 * cnt; i += GTHREADS) {
+            const int jj = i >> 1, half = i & 1;
+            const uint16_t e = bls[b0 + jj];
+            const int p = U.r0 + (e & 0xff), q = U.c0 + (e >> 8);
+            const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
+            const T2 *src = yin + 4 * (((long long)t * P.nbl + bl) * P.nchan + kk);
+            cp16(dst + 4 * jj + 2 * half, src + 2 * half);
+        }
+        cp_commit();
+    };
+    const int njobs = (k1 - k0) * nchunk;
+    if (njobs > 0) issue_y(0);
+    int job = 0;
+    for (int k = k0; k < k1; k++) {
+        const ChanF ch = reinterpret_cast<const ChanF *>(P.chan)[k];
+        __syncthreads();
+        for (int i = tid; i < nloc * SG; i += GTHREADS) {
+            T2 v = phase(rTau + i, 0, ch);
+            if (pointing) {
+                const int a = i / SG, ss = i - a * SG;
+                const int src = min(sch * SG + ss, P.nsrc - 1);
+                const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+                const T *exq = reinterpret_cast<const T *>(P.extra) + 8 * src;
+                T E, t3;
+                beam_d<T>(ch.cnu, rRho[i], E, t3);
+                v.x *= E;
+                v.y *= E;
+                T2 d;
+                d.x = t3 * ch.cnu * ch.cnu * (exq[0] - (T)ptab[2 * ant]);
+                d.y = t3 * ch.cnu * ch.cnu * (exq[1] - (T)ptab[2 * ant + 1]);
+                sE[i] = d;
+            }
+            sA[i] = v;
+        }
+        const float4 gq0 = reinterpret_cast<const float4 *>(P.gauss)[sidx[0]];
+        const float4 gq1 = reinterpret_cast<const float4 *>(P.gauss)[sidx[1]];
+        const float2 gA = pf2(gq0.x * ch.nu2, gq1.x * ch.nu2);
+        const float2 gB = pf2(gq0.y * ch.nu2, gq1.y * ch.nu2);
+        const float2 gC = pf2(gq0.z * ch.nu2, gq1.z * ch.nu2);
+        float2 acc[NACC];
+#pragma unroll
+        for (int i = 0; i < NACC; i++) acc[i] = pf2(0.f, 0.f);
+        for (int b0 = 0; b0 < nb; b0 += BLC, job++) {
+            const int cnt = min(BLC, nb - b0);
+            cp_wait_all();
+            __syncthreads();
+            if (job + 1 < njobs) issue_y(job + 1);
+            const T2 *yb = sY + (job & 1) * BLC * 4;
+#pragma unroll 2
+            for (int i = grp; i < cnt; i += NG) {
+                const float4 bb = *reinterpret_cast<const float4 *>(sB + 4 * (b0 + i));
+                const T du = bb.x, dv = bb.y, dw = bb.z;
+                const int pq = __float_as_int(bb.w);
+                const int oa = pq & 0xffff, ob = pq >> 16;
+                const float4 ap = *reinterpret_cast<const float4 *>(sA + oa + 2 * sp);
+                const float4 aq = *reinterpret_cast<const float4 *>(sA + ob + 2 * sp);
+                const float2 apr = pf2(ap.x, ap.z), api = pf2(ap.y, ap.w);
+                const float2 aqr = pf2(aq.x, aq.z), aqi = pf2(aq.y, aq.w);
+                // z = A_p conj(A_q) for both sources
+                float2 zr = __ffma2_rn(apr, aqr, __fmul2_rn(api, aqi));
+                float2 zi = __ffma2_rn(api, aqr, __fmul2_rn(pf2(-apr.x, -apr.y), aqi));
+                if (any_gauss) {
+                    const float2 e = __ffma2_rn(gA, pdup(du * du), __ffma2_rn(gB, pdup(du * dv), __fmul2_rn(gC, pdup(dv * dv))));
+                    const float2 g = pf2(exp2f(e.x), exp2f(e.y));
+                    zr = __fmul2_rn(zr, g);
+                    zi = __fmul2_rn(zi, g);
+                }
+                const float4 y01 = *reinterpret_cast<const float4 *>(yb + 4 * i);
+                const float4 y23 = *reinterpret_cast<const float4 *>(yb + 4 * i + 2);
+                const float2 nzi = pf2(-zi.x, -zi.y);
+                acc[0] = __ffma2_rn(zr, pdup(y01.x), __ffma2_rn(nzi, pdup(y01.y), acc[0]));
+                acc[1] = __ffma2_rn(zr, pdup(y01.z), __ffma2_rn(nzi, pdup(y01.w), acc[1]));
+                acc[2] = __ffma2_rn(zr, pdup(y23.x), __ffma2_rn(nzi, pdup(y23.y), acc[2]));
+                acc[3] = __ffma2_rn(zr, pdup(y23.z), __ffma2_rn(nzi, pdup(y23.w), acc[3]));
+                const float2 br = __ffma2_rn(sI, pdup(y01.x), __ffma2_rn(sQ, pdup(y01.z),
+                                  __ffma2_rn(sU, pdup(y23.x), __fmul2_rn(sV, pdup(y23.z)))));
+                const float2 bi = __ffma2_rn(sI, pdup(y01.y), __ffma2_rn(sQ, pdup(y01.w),
+                                  __ffma2_rn(sU, pdup(y23.y), __fmul2_rn(sV, pdup(y23.w)))));
+                const float2 re = __ffma2_rn(zr, br, __fmul2_rn(nzi, bi));   // z beta
+                const float2 im = __ffma2_rn(zr, bi, __fmul2_rn(zi, br));
+                acc[4] = __ffma2_rn(im, pdup(du), acc[4]);
+                acc[5] = __ffma2_rn(im, pdup(dv), acc[5]);
+                acc[6] = __ffma2_rn(im, pdup(dw), acc[6]);
+                if (any_gauss) {
+                    acc[7] = __ffma2_rn(re, pdup(du * du), acc[7]);
+                    acc[8] = __ffma2_rn(re, pdup(du * dv), acc[8]);
+                    acc[9] = __ffma2_rn(re, pdup(dv * dv), acc[9]);
+                }
+                if (pointing) {
+                    const float4 ep = *reinterpret_cast<const float4 *>(sE + oa + 2 * sp);
+                    const float4 eq = *reinterpret_cast<const float4 *>(sE + ob + 2 * sp);
+                    acc[10] = __ffma2_rn(re, pf2(ep.x + eq.x, ep.z + eq.z), acc[10]);
+                    acc[11] = __ffma2_rn(re, pf2(ep.y + eq.y, ep.w + eq.w), acc[11]);
+                }
+            }
+        }
+        const T nu = nu_of<T>(ch);
+        const T lnr = log(nu / (T)P.ref_freq_hz);
+        const T k2pi = T(2.0 * kPi / kCLight) * nu;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            T a[NACC];
+#pragma unroll
+            for (int i = 0; i < NACC; i++) a[i] = h ? acc[i].y : acc[i].x;
+            const T *ex = reinterpret_cast<const T *>(P.extra) + 8 * sidx[h];
+            const T l = ex[0], m = ex[1], l_n = ex[2], m_n = ex[3];
+            const float4 st = h ? st1 : st0;
+            T w = exp(reinterpret_cast<const T *>(P.alpha)[sidx[h]] * lnr);
+            T dlnE2_l = 0, dlnE2_m = 0;
+            if (!pointing) {
+                T E, t3;
+                beam_d<T>(ch.cnu, rRho[2 * sp + h], E, t3);
+                w *= E * E;
+                const T cnu2 = ch.cnu * ch.cnu;
+                dlnE2_l = T(2) * t3 * cnu2 * l;
+                dlnE2_m = T(2) * t3 * cnu2 * m;
+            }
+            const T aR = st.x * a[0] + st.y * a[1] + st.z * a[2] + st.w * a[3];
+            out[h][0] += (double)(w * (-k2pi * (a[4] - l_n * a[6]) + (pointing ? a[10] : aR * dlnE2_l)));
+            out[h][1] += (double)(w * (-k2pi * (a[5] - m_n * a[6]) + (pointing ? a[11] : aR * dlnE2_m)));
+            out[h][2] += (double)(w * a[0]);
+            out[h][3] += (double)(w * a[1]);
+            out[h][4] += (double)(w * a[2]);
+            out[h][5] += (double)(w * a[3]);
+            out[h][6] += (double)(w * aR * lnr);
+            if (is_gauss[h]) {
+                const T K = T(kGaussK / (kCLight * kCLight)) * nu * nu;
+                const T mj = ex[4], mi = ex[5], sps = ex[6], cps = ex[7];
+                const T dd = mj * mj - mi * mi;
+                const T Au = a[7], Auv = a[8], Av = a[9];
+                out[h][7] += (double)(w * -K * (2 * mj * sps * sps * Au + 4 * mj * sps * cps * Auv + 2 * mj * cps * cps * Av));
+                out[h][8] += (double)(w * -K * (2 * mi * cps * cps * Au - 4 * mi * sps * cps * Auv + 2 * mi * sps * sps * Av));
+                out[h][9] += (double)(w * -K * (2 * sps * cps * dd * Au + 2 * dd * (cps * cps - sps * sps) * Auv -
+                                                2 * sps * cps * dd * Av));
+            }
+        }
+    }
+    // ---- combine the baseline groups in a fixed order: one partial per source ----
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int i = 0; i < NGRAD; i++) sRed[(grp * SG + 2 * sp + h) * NGRAD + i] = out[h][i];
+    __syncthreads();
+    if (grp == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (!sact[h]) continue;
+            const long long prow = ((long long)t * P.ncg + cg) * P.nunits + u;
+            double *o = P.partials + (prow * P.nsrc + sidx[h]) * NGRAD;
+            for (int i = 0; i < NGRAD; i++) {
+                double v = 0.0;
+                for (int g = 0; g < NG; g++) v += sRed[(g * SG + 2 * sp + h) * NGRAD + i];
+                o[i] = v;
+            }
+        }
+    }
+}
+
 // Column sums of a [nrows][ncols] array in fixed order: block (x, y) sums
 // rows [y rpb, (y+1) rpb) of 32 columns with 8 row phases, then the phases.
 constexpr int RTX = 32, RTY = 8;
@@ -488,9 +740,9 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
         k_grad_src<double><<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     } else {
         const size_t smem = GSmem<float>::bytes(c->has_pointing);
-        e = cudaFuncSetAttribute(k_grad_src<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_grad_src_f32x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_grad_src<float><<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
+        k_grad_src_f32x2<<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
