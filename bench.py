@@ -202,9 +202,9 @@ def form_small_latency(torch, R):
 def form_sampler(torch, R):
     """Ensemble Metropolis over the batched observation (64 antennas, 50 t,
     32 ch): 128 chains on the 100-source sky model, each moving l, m, I and
-    alpha of its brightest source with steps near the posterior widths (the
-    data pin a 1 Jy source's position to ~1e-10 rad); one step scores all
-    128 proposals (128 x 100 sources) with one batched chi^2 call."""
+    alpha of its brightest source, the proposal widths adapted during burn-in
+    towards 30 % acceptance; one step scores all 128 proposals (128 x 100
+    sources) with one batched chi^2 call."""
     from paper_1501_07719_gb300 import sampler
     wl = rime_synth.WORKLOADS["64ant-50t-32ch-512sets"]
     inp = rime_synth.make_inputs(wl, precision="f32")
@@ -219,14 +219,15 @@ def form_sampler(torch, R):
     one[int(np.argmax(inp["sources"]["stokes"][:, 0]))] = 1.0
     steps = {"l": 1e-9 * one, "m": 1e-9 * one, "I": 1e-4 * one, "alpha": 1e-4 * one}
     s = sampler.EnsembleMetropolis(ctx, inp["sources"], 128, steps, seed=1)
-    s.run(2)
+    scale = s.adapt(24, target=0.3)
     t0 = time.perf_counter()
-    out = s.run(6)
-    dt = (time.perf_counter() - t0) / 6
+    out = s.run(8)
+    dt = (time.perf_counter() - t0) / 8
     ctx.close()
     return {"workload": wl.name + " observation, 100-source sky model", "chains": 128,
             "params_moved_per_chain": 4, "seconds_per_step": dt, "proposals_per_s": 128 / dt,
-            "accept_rate": float(out["accept"].mean()),
+            "accept_rate": float(out["accept"].mean()), "adapted_step_scale": float(scale[-1]),
+            "adaptation": "24 burn-in steps rescaling the proposal widths towards 30 % acceptance",
             "note": "wall clock per step: host proposals, one batched chi^2 (128 sets x 100 sources), "
                     "accept/reject"}
 
@@ -390,6 +391,72 @@ def form_split(torch, R):
     return res
 
 
+# Table 4: Montblanc's time (s) on a K40 for the full RIME + chi^2 at 64
+# channels, 100 timesteps, 50 point + 50 Gaussian sources: (FP32, FP64).
+K40_TABLE4_S = {7: (0.0042, 0.0073), 14: (0.0136, 0.0215), 27: (0.0435, 0.0703), 64: (0.2320, 0.3668),
+                128: (0.7007, 0.9113), 192: (1.5730, 2.3540)}
+
+
+def _sweep_time(torch, R, wl, f64, reps):
+    """Median device time (ms) of one fused chi^2 on workload wl; the data are
+    zero and the weights the workload's (the cost does not depend on values)."""
+    inp = rime_synth.make_inputs(wl, precision="f64" if f64 else "f32", noise=False)
+    cdt = torch.complex128 if f64 else torch.complex64
+    rdt = np.float64 if f64 else np.float32
+    stream = torch.cuda.current_stream()
+    D = torch.zeros((wl.ntime, wl.nbl, wl.nchan, 4), dtype=cdt, device="cuda")
+    W = torch.from_numpy(inp["weight"].astype(rdt)).cuda()
+    ctx = R.Rime(inp, R.RIME_FP64 if f64 else R.RIME_FP32, data=D, weight=W, stream=stream)
+    del D, W
+    ctx.set_gains(inp["gains"])
+    ctx.set_sources(inp["sources"])
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        ctx.chi2_async(out)
+    ctx.sync()
+    ms = _timed(torch, stream, lambda: ctx.chi2_async(out), reps)
+    ctx.close()
+    return ms
+
+
+def form_sweep(torch, R):
+    """The paper's problem-size studies on synthetic inputs of the same shapes:
+    (1) Table 4's antenna sweep (7-192 antennas, 100 timesteps, 64 channels,
+    50 point + 50 Gaussian sources) in FP32 and FP64, next to the paper's K40
+    times; (2) the dimension variation of Sec. 5 (the 7-antenna case with the
+    channels, timesteps, point or Gaussian sources multiplied), as device time
+    per source-term, which shows what a unit of each dimension costs."""
+    rows = []
+    for na in sorted(K40_TABLE4_S):
+        wl = rime_synth.custom(na, 100, 64, 50, 50, seed_index=200 + na)
+        row = {"na": na, "nbl": wl.nbl}
+        for i, (name, f64) in enumerate((("f32", False), ("f64", True))):
+            reps = 3 if (f64 and na >= 128) else 10
+            ms = _sweep_time(torch, R, wl, f64, reps)
+            row[name] = {"ms": ms, "terms_per_s": terms_of(wl) / (ms * 1e-3),
+                         "k40_s": K40_TABLE4_S[na][i], "speedup_vs_k40": K40_TABLE4_S[na][i] / (ms * 1e-3)}
+        rows.append(row)
+    base = dict(na=7, ntime=100, nchan=64, npsrc=50, ngsrc=50)
+    dims = {"nchan": [64, 128, 256, 512], "ntime": [100, 300, 600, 1000],
+            "npsrc": [50, 550, 1150, 1950], "ngsrc": [50, 550, 1150, 1950]}
+    var = {}
+    for dim, vals in dims.items():
+        pts = []
+        for v in vals:
+            kw = dict(base, **{dim: v})
+            wl = rime_synth.custom(kw["na"], kw["ntime"], kw["nchan"], kw["npsrc"], kw["ngsrc"], seed_index=260)
+            ms = _sweep_time(torch, R, wl, False, 10)
+            pts.append({dim: v, "ms": ms, "source_terms": terms_of(wl) // 4,
+                        "ns_per_source_term": ms * 1e6 / (terms_of(wl) // 4)})
+        var[dim] = pts
+    return {"antennas": {"workload": "N ant, 100 t, 64 ch, 50 pt + 50 gauss (Table 4 shapes)",
+                         "rows": rows},
+            "dimension_variation": {"workload": "7 ant, 100 t, 64 ch, 50 pt + 50 gauss, one dimension "
+                                                "multiplied (Sec. 5 dimension study), FP32", "series": var},
+            "note": "device time of one fused chi^2 (CUDA events, median); the K40 times are the paper's "
+                    "Table 4 (full RIME + chi^2 on a K40), context not target"}
+
+
 def run_only(args):
     """One form on one (possibly reduced) workload, for profiling: prints the
     median launch time. Not the benchmark line."""
@@ -467,12 +534,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the gradient, batched and split-precision comparisons")
-    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32"],
+    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep"],
                     help="time one form on --workload (optionally with fewer timesteps / channels) "
                          "instead of the benchmark; for profiling")
     ap.add_argument("--ntime", type=int, default=0)
     ap.add_argument("--nchan", type=int, default=0)
     args = ap.parse_args()
+    if args.only == "sweep":
+        import torch
+        import paper_1501_07719_gb300 as R
+        print(json.dumps(form_sweep(torch, R)), flush=True)
+        return 0
     if args.only:
         return run_only(args)
     wl = rime_synth.WORKLOADS[args.workload]
@@ -599,7 +671,8 @@ def main():
                          "gradient": form_grad(torch, R, ms_per_step),
                          "batched": form_batched(torch, R),
                          "sampler": form_sampler(torch, R),
-                         "split_precision": form_split(torch, R)}
+                         "split_precision": form_split(torch, R),
+                         "sweep": form_sweep(torch, R)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, inp)
     if rank == 0:

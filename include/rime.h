@@ -195,6 +195,27 @@ typedef enum {
  *   mode  a rime_tc_mode; RIME_E_INVALID for an RIME_FP64 context. */
 rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 
+/* Direct-sum kernels of rime_predict, rime_chi2 and rime_chi2_async
+ * (rime_set_kernel). */
+typedef enum {
+    RIME_KERNEL_AUTO = 0,     /* NARROW for arrays of up to 32 (FP32) or 45 (FP64) antennas,
+                                 else TILED (default) */
+    RIME_KERNEL_TILED = 1,    /* a block per (t, channel, antenna unit), several baselines per thread */
+    RIME_KERNEL_NARROW = 2    /* a block per (t, group of channels), one or two (baseline,
+                                 channel) pairs per thread; arrays of up to 45 antennas */
+} rime_kernel;
+
+/* Selects the kernel that evaluates the direct source sum (Algorithms 1-2
+ * fused with eqs. 1 and 7) in both precisions; the result is the same sum
+ * in another order (equal to rounding). TILED suits large arrays (each
+ * staged per-antenna factor serves a whole antenna unit); NARROW suits small
+ * ones, whose few baselines per channel would leave a tiled block nearly
+ * empty. The gradient and the batched FP32 launch always use the tiled
+ * kernel; the tensor-core modes take precedence when set.
+ *   kernel  a rime_kernel; RIME_E_INVALID for another value, or for
+ *           RIME_KERNEL_NARROW with more than 45 antennas. */
+rime_status rime_set_kernel(rime_ctx *ctx, int32_t kernel);
+
 /* Configuration of the batched FP32 launch, and the autotuner's record.
  * A work item of the persistent launch is (timestep, group of
  * channels_per_item channels, antenna unit, group of sets_per_item sets),

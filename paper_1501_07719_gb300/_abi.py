@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "librime.so")
 RIME_OK, RIME_E_INVALID, RIME_E_STATE, RIME_E_OOM, RIME_E_CUDA, RIME_E_TIMEOUT, RIME_E_NONFINITE = range(7)
 RIME_FP32, RIME_FP64 = 0, 1
 RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 = 0, 1, 2
+RIME_KERNEL_AUTO, RIME_KERNEL_TILED, RIME_KERNEL_NARROW = 0, 1, 2
 
 
 class rime_dims(C.Structure):
@@ -75,7 +76,9 @@ def lib():
         L.rime_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
-        for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode"):
+        L.rime_set_kernel.argtypes = [vp, C.c_int32]
+        for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
+                  "rime_set_kernel"):
             getattr(L, f).restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
@@ -284,6 +287,11 @@ def rime_set_batched_config(ctx, channels_per_item=None, blocks_per_sm=2, order=
         return
     c = rime_batch_config(channels_per_item, blocks_per_sm, order, sets_per_item)
     _check(lib().rime_set_batched_config(ctx, C.byref(c)), ctx)
+
+
+def rime_set_kernel(ctx, kernel: int):
+    """RIME_KERNEL_AUTO, RIME_KERNEL_TILED or RIME_KERNEL_NARROW (<= 45 antennas)."""
+    _check(lib().rime_set_kernel(ctx, int(kernel)), ctx)
 
 
 def rime_set_tensor_mode(ctx, mode: int):

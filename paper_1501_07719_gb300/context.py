@@ -87,6 +87,11 @@ class Rime:
         (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32) or the direct sum (RIME_TC_OFF)."""
         A.rime_set_tensor_mode(self.ctx, mode)
 
+    def set_kernel(self, kernel: int):
+        """Direct-sum kernel: RIME_KERNEL_AUTO (default), RIME_KERNEL_TILED or
+        RIME_KERNEL_NARROW (arrays of up to 45 antennas)."""
+        A.rime_set_kernel(self.ctx, kernel)
+
     def batched_config(self) -> dict:
         return A.rime_batched_config(self.ctx)
 

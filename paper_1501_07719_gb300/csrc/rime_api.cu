@@ -377,7 +377,7 @@ rime_status rime_predict(rime_ctx *c, void *vis_out) {
     if (!vis_out) return fail(c, RIME_E_INVALID, "vis_out is NULL");
     if (!c->sources_set) return fail(c, RIME_E_STATE, "rime_set_sources has not been called");
     if (c->tc_mode != RIME_TC_OFF) CK(c, launch_split(c, true, vis_out, nullptr), "tensor-core predict kernel");
-    else CK(c, launch_fused(c, vis_out, nullptr, false), "predict kernel");
+    else CK(c, launch_fused_auto(c, vis_out, nullptr, false), "predict kernel");
     return RIME_OK;
 }
 
@@ -387,7 +387,7 @@ rime_status rime_chi2_async(rime_ctx *c, double *chi2_dev) {
     if (!c->sources_set) return fail(c, RIME_E_STATE, "rime_set_sources has not been called");
     if (!c->has_data) return fail(c, RIME_E_STATE, "no observed data (rime_set_data)");
     if (c->tc_mode != RIME_TC_OFF) CK(c, launch_split(c, false, nullptr, chi2_dev), "tensor-core chi2 kernel");
-    else CK(c, launch_fused(c, nullptr, chi2_dev, true), "chi2 kernel");
+    else CK(c, launch_fused_auto(c, nullptr, chi2_dev, true), "chi2 kernel");
     return RIME_OK;
 }
 
@@ -399,6 +399,16 @@ rime_status rime_set_tensor_mode(rime_ctx *c, int32_t mode) {
         return fail(c, RIME_E_INVALID, "the tensor-core modes need an RIME_FP32 context");
     c->tc_mode = mode;
     CK(c, reset_class(c, EC_MODE), "reset status");
+    return RIME_OK;
+}
+
+rime_status rime_set_kernel(rime_ctx *c, int32_t kernel) {
+    if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
+    if (kernel != RIME_KERNEL_AUTO && kernel != RIME_KERNEL_TILED && kernel != RIME_KERNEL_NARROW)
+        return fail(c, RIME_E_INVALID, "kernel must be RIME_KERNEL_AUTO, RIME_KERNEL_TILED or RIME_KERNEL_NARROW");
+    if (kernel == RIME_KERNEL_NARROW && c->dims.na > NARROW_MAX_NA)
+        return fail(c, RIME_E_INVALID, "RIME_KERNEL_NARROW takes arrays of at most 45 antennas");
+    c->kernel = kernel;
     return RIME_OK;
 }
 

@@ -193,7 +193,9 @@ rime_status rime_chi2_batched(rime_ctx *c, int32_t nsets, const int32_t *off, co
 
     if (c->dims.precision == RIME_FP64) {
         for (int j = 0; j < nsets; j++)
-            CKB(c, launch_fused_f64_range(c, off[j], off[j + 1], chi2_dev + j), "batched FP64 kernel");
+            CKB(c, narrow_applies(c) ? launch_narrow(c, MODE_CHI2, nullptr, chi2_dev + j, off[j], off[j + 1])
+                                     : launch_fused_f64_range(c, off[j], off[j + 1], chi2_dev + j),
+                "batched FP64 kernel");
         return RIME_OK;
     }
 

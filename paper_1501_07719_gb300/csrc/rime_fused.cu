@@ -27,6 +27,7 @@
 // kernel issues no FP64 instruction outside the final reduction.
 #include "rime_internal.cuh"
 #include "rime_dev.cuh"
+#include "rime_fused_common.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -36,12 +37,6 @@ namespace rime {
 // ===========================================================================
 // Shared device helpers
 // ===========================================================================
-__device__ __forceinline__ float ex2_approx(float e) {
-    float g;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
-    return g;
-}
-
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
@@ -56,48 +51,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Block-wide deterministic FP64 sum of one value per thread; result valid in
-// thread 0. red: >= 32 doubles of shared memory.
-template <int THREADS>
-__device__ __forceinline__ double block_sum(double v, double *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double x = 0.0;
-    if (warp == 0) {
-        x = lane < THREADS / 32 ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    }
-    return x;
-}
-
-// One partial per block, then the last block to arrive sums them in index
-// order and stores the total. All threads of the block must call it.
-template <int THREADS>
-__device__ void finish_chi2(double block_value, const FusedParams &P, double *red, int *sLast) {
-    if (threadIdx.x == 0) {
-        P.partials[blockIdx.x] = block_value;
-        __threadfence();
-        unsigned ticket = atomicAdd(P.counter, 1u);
-        *sLast = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (*sLast) {
-        __threadfence();
-        double s = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) s += __ldcg(&P.partials[i]);
-        double tot = block_sum<THREADS>(s, red);
-        if (threadIdx.x == 0) {
-            *P.result = tot;
-            *P.counter = 0u;
-        }
-    }
-}
 
 // Adjoint of the chi^2 term of one visibility (eq. 7 through eq. 1):
 //   Sh = 2 w G_p^H R G_q with R = V - D; for a source with coherency c B0
@@ -401,27 +354,6 @@ struct Smem {
     float GG[NLOC * 8];         // gradient mode: per-antenna gains gradient of this block
     double red[32];
 };
-
-// Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
-// nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small
-// products add the rest; the result is reduced to about [-1/2, 1/2] turns,
-// where the SFU sine and cosine are accurate to ~2^-21 absolute.
-__device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
-    float p = ch.nu_hi * tau.x;
-    float e = fmaf(ch.nu_hi, tau.x, -p);
-    float r = p - round_int_f(p);
-    float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
-    float sn, cs;
-    __sincosf(6.28318530717958648f * f, &sn, &cs);
-    return make_float2(cs, sn);
-}
-
-// Beam E = cos^3(C nu[GHz] rho) (eq. 4), zero past the first null.
-__device__ __forceinline__ float beam(float rho, const ChanF &ch) {
-    float x = ch.cnu * rho;
-    float cb = cosf(x);
-    return (x < 1.57079632679f) ? cb * cb * cb : 0.0f;
-}
 
 // Local (row, column) antennas of slot j of a thread tile; rev = 1 when the
 // tile forms the pair in the order (column, row) and the accumulated sums
@@ -958,7 +890,7 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
     return launch_fused_mode(c, chi2 ? MODE_CHI2 : MODE_PREDICT, vis_out, result, nullptr, nullptr);
 }
 
-static void fill_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
+void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
                         double *grad_gains) {
     P.na = c->dims.na;
     P.ntime = c->dims.ntime;
@@ -998,7 +930,7 @@ static void fill_params(const rime_ctx *c, FusedParams &P, void *vis_out, double
 cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
                               double *grad_gains) {
     FusedParams P{};
-    fill_params(c, P, vis_out, result, yout, grad_gains);
+    fill_fused_params(c, P, vis_out, result, yout, grad_gains);
     int blocks = fused_blocks(c);
     if (blocks == 0) return cudaSuccess;
     if (c->dims.precision == RIME_FP64) {
@@ -1019,7 +951,7 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
 
 cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid) {
     FusedParams P{};
-    fill_params(c, P, nullptr, nullptr, nullptr, nullptr);
+    fill_fused_params(c, P, nullptr, nullptr, nullptr, nullptr);
     if (grid <= 0 || B.nitems == 0) return cudaSuccess;
     const size_t sm = sizeof(f32::Smem);
     cudaError_t e = cudaFuncSetAttribute(f32::k_batched_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1047,7 +979,7 @@ cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *p
 
 cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result) {
     FusedParams P{};
-    fill_params(c, P, nullptr, result, nullptr, nullptr);
+    fill_fused_params(c, P, nullptr, result, nullptr, nullptr);
     P.src0 = src0;
     P.src1 = src1;
     const int blocks = fused_blocks(c);

@@ -1,0 +1,83 @@
+// rime_fused_common.cuh -- device pieces shared by the fused predict + chi^2
+// kernels (the tiled kernels of rime_fused.cu and the small-array kernel of
+// rime_narrow.cu): the FP32 phase and beam factors and the deterministic
+// chi^2 reduction.
+#pragma once
+#include "rime_internal.cuh"
+#include "rime_dev.cuh"
+
+namespace rime {
+
+__device__ __forceinline__ float ex2_approx(float e) {
+    float g;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(g) : "f"(e));
+    return g;
+}
+
+// Block-wide deterministic FP64 sum of one value per thread; result valid in
+// thread 0. red: >= 32 doubles of shared memory.
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double x = 0.0;
+    if (warp == 0) {
+        x = lane < THREADS / 32 ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    }
+    return x;
+}
+
+// One partial per block, then the last block to arrive sums them in index
+// order and stores the total. All threads of the block must call it.
+template <int THREADS>
+__device__ void finish_chi2(double block_value, const FusedParams &P, double *red, int *sLast) {
+    if (threadIdx.x == 0) {
+        P.partials[blockIdx.x] = block_value;
+        __threadfence();
+        unsigned ticket = atomicAdd(P.counter, 1u);
+        *sLast = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (*sLast) {
+        __threadfence();
+        double s = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += THREADS) s += __ldcg(&P.partials[i]);
+        double tot = block_sum<THREADS>(s, red);
+        if (threadIdx.x == 0) {
+            *P.result = tot;
+            *P.counter = 0u;
+        }
+    }
+}
+
+namespace f32 {
+// Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
+// nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small
+// products add the rest; the result is reduced to about [-1/2, 1/2] turns,
+// where the SFU sine and cosine are accurate to ~2^-21 absolute.
+__device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
+    float p = ch.nu_hi * tau.x;
+    float e = fmaf(ch.nu_hi, tau.x, -p);
+    float r = p - round_int_f(p);
+    float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
+    float sn, cs;
+    __sincosf(6.28318530717958648f * f, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+// Beam E = cos^3(C nu[GHz] rho) (eq. 4), zero past the first null.
+__device__ __forceinline__ float beam(float rho, const ChanF &ch) {
+    float x = ch.cnu * rho;
+    float cb = cosf(x);
+    return (x < 1.57079632679f) ? cb * cb * cb : 0.0f;
+}
+
+}  // namespace f32
+
+}  // namespace rime

@@ -212,6 +212,7 @@ struct rime_ctx {
     int nsm = 0;
     // tensor-core split-precision mode (FP32 contexts)
     int tc_mode = 0;                  // rime_tc_mode
+    int kernel = 0;                   // rime_kernel
     int2 *d_stiles = nullptr;         // its tiles (p0, q0)
     int nstiles = 0;
     double *d_spart = nullptr;        // one partial chi^2 per block
@@ -245,6 +246,15 @@ cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid);
 int batched_blocks_per_sm();
 cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *partials, double *chi2);
 cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result);
+void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
+                       double *grad_gains);
+// rime_narrow.cu: the small-array kernel (one thread per baseline and channel)
+constexpr int NARROW_MAX_NA = 45;      // it takes arrays of up to this many antennas (990 baselines)
+constexpr int NARROW_AUTO_NA_F32 = 32; // RIME_KERNEL_AUTO picks it up to here in FP32 (FP64: 45)
+bool narrow_applies(const rime_ctx *c);
+cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1);
+// predict (chi2 = false) or chi^2 over all sources with the kernel that suits the array
+cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool chi2);
 // rime_split.cu
 cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result);
 // rime_api.cu: clears one error class of the status block (stream-ordered)

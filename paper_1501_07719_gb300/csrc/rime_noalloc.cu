@@ -209,7 +209,7 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     CKN(launch_validate_data(&c));
     if (gains) CKN(launch_convert_gains(&c));
     CKN(launch_prep_sources(&c));
-    CKN(launch_fused(&c, nullptr, chi2_dev, true));
+    CKN(launch_fused_auto(&c, nullptr, chi2_dev, true));
 
     // Wait and report the input checks; the status lives in the scratch too.
     DevStatus st;

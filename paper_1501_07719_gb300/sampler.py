@@ -113,6 +113,22 @@ class EnsembleMetropolis:
         self.nstep += 1
         return accept
 
+    def adapt(self, nsteps: int, target: float = 0.3, gain: float = 1.0) -> np.ndarray:
+        """Burn-in steps that rescale every proposal standard deviation by one
+        common factor after each step, log f = gain (a - target) / sqrt(i + 1)
+        with a the fraction of chains that accepted at step i (a stochastic
+        approximation to the scale whose acceptance rate is `target`). The
+        chains are not Markov while this runs: use it before sampling.
+        Returns the cumulative scale after each step."""
+        total, hist = 1.0, []
+        for i in range(nsteps):
+            a = float(self.step().mean())
+            f = float(np.exp(gain * (a - target) / np.sqrt(i + 1.0)))
+            self.steps = {p: s * f for p, s in self.steps.items()}
+            total *= f
+            hist.append(total)
+        return np.array(hist)
+
     def run(self, nsteps: int, thin: int = 1) -> dict:
         """nsteps steps; returns the chi^2 trace [nsteps, K], the accept trace
         and every `thin`-th state of the moved parameters."""

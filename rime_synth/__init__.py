@@ -129,10 +129,12 @@ def draw_sources(rs: dict, n: int, gauss_mask) -> dict:
 
 
 def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = None,
-                pointing_sigma: float = 0.0, time_varying: bool = False) -> dict:
+                pointing_sigma: float = 0.0, time_varying: bool = False, noise: bool = True) -> dict:
     """All inputs of one workload except the observed data (see ``observe``).
 
-    precision "f32" rounds every real input to float32 values.
+    precision "f32" rounds every real input to float32 values. noise=False
+    leaves the noise out (None; the other arrays are unchanged, every array
+    has its own stream), for timing runs that do not need the data values.
     """
     if isinstance(wl, str):
         wl = WORKLOADS[wl]
@@ -150,8 +152,11 @@ def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = N
     gains = np.broadcast_to(np.eye(2), (nt, na, nc, 2, 2)).astype(np.complex128)
     gains = gains + (rs["gains"].normal(0.0, 0.05, size=(nt, na, nc, 2, 2))
                      + 1j * rs["gains"].normal(0.0, 0.05, size=(nt, na, nc, 2, 2)))
-    noise = (rs["noise"].normal(0.0, 0.01, size=(nt, nbl, nc, 4))
-             + 1j * rs["noise"].normal(0.0, 0.01, size=(nt, nbl, nc, 4)))
+    if noise:
+        noise = (rs["noise"].normal(0.0, 0.01, size=(nt, nbl, nc, 4))
+                 + 1j * rs["noise"].normal(0.0, 0.01, size=(nt, nbl, nc, 4)))
+    else:
+        noise = None
     if wl.unit_weights:
         weight = np.ones((nt, nbl, nc))
     else:
@@ -185,7 +190,8 @@ def draw_sets(rs: dict, wl: Workload) -> dict:
 def round_f32(inp: dict) -> dict:
     out = dict(inp)
     for k in ("uvw", "freq", "gains", "noise", "weight"):
-        out[k] = _r32(inp[k])
+        if inp[k] is not None:
+            out[k] = _r32(inp[k])
     out["ref_freq_hz"] = float(_r32(inp["ref_freq_hz"]))
     if inp.get("pointing") is not None:
         out["pointing"] = _r32(inp["pointing"])

@@ -39,8 +39,13 @@ def gpu_ctx(inp, precision):
     return r
 
 
-def gpu_run(inp, precision):
+def gpu_run(inp, precision, kernel=None):
+    """Predict and chi^2 on the GPU; kernel: None (the library's choice),
+    "tiled" or "narrow"."""
+    import paper_1501_07719_gb300 as R
     r = gpu_ctx(inp, precision)
+    if kernel is not None:
+        r.set_kernel({"tiled": R.RIME_KERNEL_TILED, "narrow": R.RIME_KERNEL_NARROW}[kernel])
     V = r.predict().cpu().numpy()
     chi = r.chi2() if inp.get("data") is not None else None
     r.close()

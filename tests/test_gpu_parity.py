@@ -31,14 +31,31 @@ CASES = {
     "70ant-units": dict(wl=rime_synth.custom(70, 2, 3, 6, 5, seed_index=22), pointing_sigma=0.002),
     # a single baseline, channel and timestep
     "2ant-min": dict(wl=rime_synth.custom(2, 1, 1, 1, 0, seed_index=23)),
+    # narrow kernel shapes: 3 baselines x 70 channels (two channel groups of
+    # up to 64), Gaussians and pointing errors
+    "3ant-70ch": dict(wl=rime_synth.custom(3, 2, 70, 5, 4, seed_index=31), pointing_sigma=0.002),
+    # 23..32 antennas: one channel per block, two pairs per thread; 40 sources
+    # span three FP64 chunks (16) and two FP32 chunks (32) with ragged tails
+    "27ant-2pairs": dict(wl=rime_synth.custom(27, 2, 3, 22, 18, seed_index=32), time_varying=True),
+    "32ant": dict(wl=rime_synth.custom(32, 1, 2, 3, 3, seed_index=33), pointing_sigma=0.001),
+    # 33..45 antennas: 512-thread blocks of two pairs each (45: the largest)
+    "45ant-max": dict(wl=rime_synth.custom(45, 2, 2, 17, 5, seed_index=35), pointing_sigma=0.001),
 }
 
 
+# the kernels a case runs through: the library's choice, and each direct-sum
+# kernel that takes the array (the narrow one up to 45 antennas)
+KERNELS = [None, "tiled", "narrow"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_predict_and_chi2_match_oracle(case, precision):
+def test_predict_and_chi2_match_oracle(case, precision, kernel):
     inp = make_case(precision=precision, **CASES[case])
-    V, chi = gpu_run(inp, precision)
+    if kernel == "narrow" and inp["na"] > 45:
+        pytest.skip("the narrow kernel takes arrays of up to 45 antennas")
+    V, chi = gpu_run(inp, precision, kernel)
     Vref = inp["oracle_vis"]
     assert V.shape == Vref.shape
     assert vis_err(V, Vref) <= TOL[precision]["vis"], vis_err(V, Vref)
@@ -75,6 +92,33 @@ def test_chi2_is_deterministic(precision):
     r = gpu_ctx(inp, precision)
     a, b = r.chi2(), r.chi2()
     assert a == b
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_table4_7ant_full_size(precision):
+    # the antenna sweep's smallest array at its full size (100 timesteps, 64
+    # channels, 50 point + 50 Gaussian sources), element by element, through
+    # the kernel the library picks for it (the narrow one) and the tiled one
+    inp = make_case(rime_synth.custom(7, 100, 64, 50, 50, seed_index=207), precision)
+    cref = oracle_chi2(inp)
+    for kernel in (None, "tiled"):
+        V, chi = gpu_run(inp, precision, kernel)
+        assert vis_err(V, inp["oracle_vis"]) <= TOL[precision]["vis"], (kernel, vis_err(V, inp["oracle_vis"]))
+        assert rel_err(chi, cref) <= TOL[precision]["chi2"], (kernel, chi, cref)
+
+
+def test_kernel_choice_is_validated():
+    import paper_1501_07719_gb300 as R
+    inp = make_case(rime_synth.custom(46, 1, 1, 1, 0, seed_index=34), "f64")
+    r = gpu_ctx(inp, "f64")
+    with pytest.raises(R.RimeError) as e:
+        r.set_kernel(R.RIME_KERNEL_NARROW)
+    assert "45 antennas" in str(e.value)
+    with pytest.raises(R.RimeError):
+        r.set_kernel(7)
+    r.set_kernel(R.RIME_KERNEL_TILED)
+    r.set_kernel(R.RIME_KERNEL_AUTO)
     r.close()
 
 

@@ -49,6 +49,18 @@ def test_chains_sample_a_gaussian_posterior():
     assert 0.2 < rate < 0.7
 
 
+@pytest.mark.parametrize("start", [1e-3, 1e3])
+def test_adapt_brings_the_acceptance_rate_near_its_target(start):
+    # proposal widths 1000x too small (accept ~1) or too large (accept ~0)
+    mu, sigma = 2e-3, 5e-4
+    f = lambda models: np.array([np.sum(((m["lm"][:, 0] - mu) / sigma) ** 2) for m in models])
+    s = sampler.EnsembleMetropolis(None, _sky(2), 64, {"l": start * sigma}, seed=7, chi2_fn=f)
+    scale = s.adapt(150, target=0.3)
+    assert scale.shape == (150,)
+    rate = s.run(200)["accept"].mean()
+    assert 0.15 < rate < 0.5, rate
+
+
 def test_unknown_parameter_is_rejected():
     with pytest.raises(ValueError):
         sampler.EnsembleMetropolis(None, _sky(), 2, {"flux": 1.0}, seed=0, chi2_fn=lambda m: np.zeros(len(m)))
