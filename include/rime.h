@@ -195,6 +195,32 @@ typedef enum {
  *   mode  a rime_tc_mode; RIME_E_INVALID for an RIME_FP64 context. */
 rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 
+/* chi^2 (eq. 7, without the ln-weight term) of an observation whose data
+ * and weights stay in host memory, streamed to the GPU in chunks of
+ * chunk_ntime timesteps (the time subdivision of Sec. 4.4): while the fused
+ * kernel reduces one chunk, the next is copied on a second stream into the
+ * other of two device buffers, and the chunk values are added in chunk order.
+ * Device memory for the data is two chunks, not the observation: an
+ * observation larger than the GPU fits. The context's uvw, gains and sources
+ * cover the whole observation; its own data buffer is not used (the context
+ * may be created with data = NULL). The tensor-core modes do not apply.
+ *   data         [ntime][nbl][nchan][4] complex, host memory (pinned memory
+ *                lets the copies overlap the kernels; pageable works, without
+ *                overlap) or device memory
+ *   weight       [ntime][nbl][nchan] real, or NULL (unit weights)
+ *   chunk_ntime  timesteps per chunk; <= 0: rime_stream_chunk_ntime(ctx)
+ *   chi2         out: host pointer
+ * Waits for the result. Each chunk's data and weights are checked on the GPU
+ * as they arrive: NaN/Inf gives RIME_E_NONFINITE, a negative weight
+ * RIME_E_INVALID (the index in the message is the visibility's in the whole
+ * observation); such an error concerns this call only. */
+rime_status rime_chi2_streamed(rime_ctx *ctx, const void *data, const void *weight, int32_t chunk_ntime,
+                               double *chi2);
+
+/* The chunk length rime_chi2_streamed picks: about four waves of the fused
+ * kernel per chunk, at most ntime. 0 for a NULL context. */
+int32_t rime_stream_chunk_ntime(const rime_ctx *ctx);
+
 /* Direct-sum kernels of rime_predict, rime_chi2 and rime_chi2_async
  * (rime_set_kernel). */
 typedef enum {

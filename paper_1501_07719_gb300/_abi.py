@@ -77,8 +77,10 @@ def lib():
         L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
         L.rime_set_kernel.argtypes = [vp, C.c_int32]
+        L.rime_chi2_streamed.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
+        L.rime_stream_chunk_ntime.argtypes, L.rime_stream_chunk_ntime.restype = [vp], C.c_int32
         for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
-                  "rime_set_kernel"):
+                  "rime_set_kernel", "rime_chi2_streamed"):
             getattr(L, f).restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
@@ -287,6 +289,22 @@ def rime_set_batched_config(ctx, channels_per_item=None, blocks_per_sm=2, order=
         return
     c = rime_batch_config(channels_per_item, blocks_per_sm, order, sets_per_item)
     _check(lib().rime_set_batched_config(ctx, C.byref(c)), ctx)
+
+
+def rime_chi2_streamed(ctx, precision, data, weight=None, chunk_ntime: int = 0) -> float:
+    """chi^2 of data / weights in host (ideally pinned) or device memory, copied
+    to the GPU in chunks of chunk_ntime timesteps overlapped with the kernel
+    (0: the library's choice)."""
+    cd, rd = _ctype(precision)
+    k = _Keep()
+    out = C.c_double(0.0)
+    _check(lib().rime_chi2_streamed(ctx, k.ptr(data, cd, "data"), k.ptr(weight, rd, "weight"), int(chunk_ntime),
+                                    C.byref(out)), ctx)
+    return out.value
+
+
+def rime_stream_chunk_ntime(ctx) -> int:
+    return int(lib().rime_stream_chunk_ntime(ctx))
 
 
 def rime_set_kernel(ctx, kernel: int):

@@ -58,6 +58,15 @@ class Rime:
         A.rime_chi2_async(self.ctx, out)
         return out
 
+    def chi2_streamed(self, data, weight=None, chunk_ntime: int = 0) -> float:
+        """chi^2 of an observation whose data / weights stay in host memory
+        (pinned torch tensors overlap the copies with the kernel), streamed
+        in chunks of chunk_ntime timesteps (0: the library's choice)."""
+        return A.rime_chi2_streamed(self.ctx, self.precision, data, weight, chunk_ntime)
+
+    def stream_chunk_ntime(self) -> int:
+        return A.rime_stream_chunk_ntime(self.ctx)
+
     def chi2_grad(self, want_gains: bool = True):
         """chi^2, d chi^2 / d(source parameters) as a [nsrc, 10] float64 device
         tensor (l, m, I, Q, U, V, alpha, major, minor, pa) and, if requested,

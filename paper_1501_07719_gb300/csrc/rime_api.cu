@@ -65,9 +65,13 @@ void free_all(rime_ctx *c) {
                     c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho, c->d_units,
                     c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
                     c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
-                    c->d_spart, c->d_scounter, c->d_sscale};
+                    c->d_spart, c->d_scounter, c->d_sscale, c->d_sbuf[0], c->d_sbuf[1], c->d_schi};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    cudaEvent_t evs[] = {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->h_status) cudaFreeHost(c->h_status);
 }
 
@@ -104,6 +108,7 @@ const char *class_name(int cls) {
         case EC_GAINS: return "gains";
         case EC_SRC: return "sources";
         case EC_MODE: return "sources (tensor-core mode)";
+        case EC_SDATA: return "streamed data/weight";
         default: return "kernel";
     }
 }
@@ -133,13 +138,19 @@ rime_status sync_status(rime_ctx *c) {
             return fail(c, RIME_E_NONFINITE, buf);
         }
         const char *why = cls == EC_SRC ? "l^2+m^2 >= 1, or not major >= minor >= 0"
-                          : cls == EC_DATA ? "negative weight"
+                          : (cls == EC_DATA || cls == EC_SDATA) ? "negative weight"
                           : cls == EC_FREQ ? "frequency <= 0" : "value out of range";
         std::snprintf(buf, sizeof buf, "%s: %s (first at element %lld)", class_name(cls), why, idx);
         return fail(c, RIME_E_INVALID, buf);
     }
     return RIME_OK;
 }
+
+}  // namespace
+
+rime_status rime::sync_status_ctx(rime_ctx *c) { return sync_status(c); }
+
+namespace {
 
 size_t vis_count(const rime_ctx *c) { return (size_t)c->dims.ntime * c->nbl * c->dims.nchan; }
 

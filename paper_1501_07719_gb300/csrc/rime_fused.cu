@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     const int u = blockIdx.x % P.nunits;
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
-    const int t = rest / P.nchan;
+    const int t = P.t_begin + rest / P.nchan;
     const Unit U = P.units[u];
     const bool active = tid < U.nbody;
     const ChanD ch = reinterpret_cast<const ChanD *>(P.chan)[k];
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int u = blockIdx.x % P.nunits;
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
-    const int t = rest / P.nchan;
+    const int t = P.t_begin + rest / P.nchan;
     const double bsum = fused_item<MODE>(P, S, t, k, u, 0, P.nsrc);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
 }
@@ -925,14 +925,20 @@ void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double 
     P.grad_gains = grad_gains;
     P.src0 = 0;
     P.src1 = c->nsrc;
+    P.t_begin = 0;
 }
 
 cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
                               double *grad_gains) {
     FusedParams P{};
     fill_fused_params(c, P, vis_out, result, yout, grad_gains);
-    int blocks = fused_blocks(c);
-    if (blocks == 0) return cudaSuccess;
+    return launch_tiled_params(c, mode, P, fused_blocks(c));
+}
+
+cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long nblocks) {
+    if (nblocks == 0) return cudaSuccess;
+    if (nblocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // one partial per block
+    const int blocks = (int)nblocks;
     if (c->dims.precision == RIME_FP64) {
         size_t sm = f64::smem_bytes();
         switch (mode) {

@@ -35,7 +35,11 @@ constexpr double kLog2e = 1.4426950408889634;
 // is set again.
 // EC_RUN: a kernel gave up a bounded wait (reported once, then cleared);
 // EC_MODE: the sources do not suit the tensor-core mode (Gaussian sources).
-enum ErrClass { EC_FREQ = 0, EC_UVW = 1, EC_DATA = 2, EC_GAINS = 3, EC_SRC = 4, EC_RUN = 5, EC_MODE = 6, EC_N = 8 };
+enum ErrClass {
+    EC_FREQ = 0, EC_UVW = 1, EC_DATA = 2, EC_GAINS = 3, EC_SRC = 4, EC_RUN = 5, EC_MODE = 6,
+    EC_SDATA = 7,   // data / weights of a streamed chi^2 (checked per chunk, cleared per call)
+    EC_N = 8
+};
 enum ErrBits : int {
     EB_NONFINITE = 1,
     EB_RANGE = 2,       // value outside its domain (l^2+m^2 >= 1, w < 0, nu <= 0, axes)
@@ -115,6 +119,7 @@ struct FusedParams {
     void *yout;                // complex T [ntime][nbl][nchan][4]: Stokes-projected adjoint Y_X
     double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
     int src0, src1;            // FP64 kernel: the source range [src0, src1) of this launch
+    int t_begin;               // first timestep of the launch (the grid covers a time range)
 };
 
 // Batched chi^2: the schedule of a persistent launch. Work item i is
@@ -138,7 +143,7 @@ __device__ __forceinline__ bool inputs_bad(const DevStatus *st) {
     int e = 0;
 #pragma unroll
     for (int i = 0; i < EC_RUN; i++) e |= st->err[i];
-    return (e | st->err[EC_MODE]) != 0;
+    return (e | st->err[EC_MODE] | st->err[EC_SDATA]) != 0;
 }
 
 }  // namespace rime
@@ -213,6 +218,13 @@ struct rime_ctx {
     // tensor-core split-precision mode (FP32 contexts)
     int tc_mode = 0;                  // rime_tc_mode
     int kernel = 0;                   // rime_kernel
+    // streamed chi^2 (rime_stream.cu): a copy stream, two chunk buffers
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    void *d_sbuf[2] = {nullptr, nullptr};   // chunk data, then chunk weights
+    size_t sbuf_cap = 0;                     // bytes of each buffer
+    double *d_schi = nullptr;                // chi^2 of each chunk
+    size_t schi_cap = 0;
     int2 *d_stiles = nullptr;         // its tiles (p0, q0)
     int nstiles = 0;
     double *d_spart = nullptr;        // one partial chi^2 per block
@@ -233,6 +245,10 @@ cudaError_t launch_convert_gains(rime_ctx *c);
 cudaError_t launch_prep_sources(rime_ctx *c);
 cudaError_t launch_prep_delays(rime_ctx *c);
 cudaError_t launch_ln_norm(rime_ctx *c);
+// checks nvis visibilities' data / weights (either may be NULL) and flags class
+// cls with the index i0 + i of the first bad one
+cudaError_t launch_validate_chunk(rime_ctx *c, long long nvis, const void *data, const void *weight, int cls,
+                                  long long i0);
 // rime_grad.cu
 cudaError_t launch_grad_src(rime_ctx *c, double *grad_src);
 // launchers (rime_fused.cu)
@@ -248,11 +264,15 @@ cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *p
 cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result);
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
                        double *grad_gains);
+// launches the tiled fused kernel of `mode` with prepared parameters over `blocks` blocks
+cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long blocks);
 // rime_narrow.cu: the small-array kernel (one thread per baseline and channel)
 constexpr int NARROW_MAX_NA = 45;      // it takes arrays of up to this many antennas (990 baselines)
 constexpr int NARROW_AUTO_NA_F32 = 32; // RIME_KERNEL_AUTO picks it up to here in FP32 (FP64: 45)
 bool narrow_applies(const rime_ctx *c);
 cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1);
+// the same with prepared parameters over timesteps [P.t_begin, P.t_begin + nt)
+cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt);
 // predict (chi2 = false) or chi^2 over all sources with the kernel that suits the array
 cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool chi2);
 // rime_split.cu
@@ -264,6 +284,8 @@ void set_global_error(const char *msg);
 // error reporting and the allocation cap shared by the entry points (rime_api.cu)
 rime_status fail_ctx(rime_ctx *c, rime_status s, const std::string &msg);
 rime_status cuda_fail_ctx(rime_ctx *c, cudaError_t e, const char *what);
+// waits for the context's stream and turns the device status block into a status
+rime_status sync_status_ctx(rime_ctx *c);
 size_t alloc_cap();
 
 // Device allocations of one context call; RIME_TEST_MAX_BYTES caps their sum,

@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
 
     if (inputs_bad(P.status)) return;
     const int tid = threadIdx.x;
-    const int t = blockIdx.x / ngroups;
-    const int k0 = (blockIdx.x - t * ngroups) * cg;
+    const int tl = blockIdx.x / ngroups;
+    const int t = P.t_begin + tl;
+    const int k0 = (blockIdx.x - tl * ngroups) * cg;
     const int ncg = min(cg, P.nchan - k0);
     const int nbl = (int)P.nbl;
     const Chan *chan = reinterpret_cast<const Chan *>(P.chan);
@@ -321,13 +322,17 @@ bool narrow_applies(const rime_ctx *c) {
 }
 
 cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1) {
-    using namespace narrow;
     FusedParams P{};
     fill_fused_params(c, P, vis_out, result, nullptr, nullptr);
     P.src0 = src0;
     P.src1 = src1;
+    return launch_narrow_params(c, mode, P, c->dims.ntime);
+}
+
+cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt) {
+    using namespace narrow;
     const Shape s = shape_for(c->dims.na, c->dims.nchan);
-    const long long blocks = (long long)c->dims.ntime * s.ngroups;
+    const long long blocks = (long long)nt * s.ngroups;
     if (blocks == 0) return cudaSuccess;
     if (blocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // cannot happen: <= fused blocks
     const bool f64 = c->dims.precision == RIME_FP64;

@@ -59,7 +59,8 @@ __global__ void k_validate_uvw(long long n_ta, const double *uvw, const double *
 }
 
 template <typename T>
-__global__ void k_validate_data(long long nvis, const T *data, const T *weight, DevStatus *st) {
+__global__ void k_validate_data(long long nvis, const T *data, const T *weight, DevStatus *st, int cls,
+                                long long i0) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nvis) return;
     bool ok = true;
@@ -70,9 +71,9 @@ __global__ void k_validate_data(long long nvis, const T *data, const T *weight, 
     if (weight) {
         T w = weight[i];
         if (!isfinite(w)) ok = false;
-        else if (w < T(0)) flag(st, EC_DATA, EB_RANGE, i);
+        else if (w < T(0)) flag(st, cls, EB_RANGE, i0 + i);
     }
-    if (!ok) flag(st, EC_DATA, EB_NONFINITE, i);
+    if (!ok) flag(st, cls, EB_NONFINITE, i0 + i);
 }
 
 // complex128 gains -> compute precision; checks finiteness.
@@ -217,15 +218,19 @@ cudaError_t launch_validate_uvw(rime_ctx *c) {
 
 cudaError_t launch_validate_data(rime_ctx *c) {
     long long nvis = (long long)c->dims.ntime * c->nbl * c->dims.nchan;
+    return launch_validate_chunk(c, nvis, c->has_data ? c->d_data : nullptr, c->has_weight ? c->d_weight : nullptr,
+                                 EC_DATA, 0);
+}
+
+cudaError_t launch_validate_chunk(rime_ctx *c, long long nvis, const void *data, const void *weight, int cls,
+                                  long long i0) {
     if (nvis == 0) return cudaSuccess;
     if (c->dims.precision == RIME_FP64)
         k_validate_data<double><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
-            nvis, c->has_data ? (const double *)c->d_data : nullptr,
-            c->has_weight ? (const double *)c->d_weight : nullptr, c->d_status);
+            nvis, (const double *)data, (const double *)weight, c->d_status, cls, i0);
     else
         k_validate_data<float><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
-            nvis, c->has_data ? (const float *)c->d_data : nullptr,
-            c->has_weight ? (const float *)c->d_weight : nullptr, c->d_status);
+            nvis, (const float *)data, (const float *)weight, c->d_status, cls, i0);
     return cudaGetLastError();
 }
 

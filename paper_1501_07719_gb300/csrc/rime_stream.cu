@@ -1,0 +1,155 @@
+// rime_stream.cu -- rime_chi2_streamed: chi^2 (eq. 7) of an observation whose
+// data and weights stay in host memory, in time chunks (Sec. 4.4).
+//
+// The paper subdivides a problem that does not fit the GPU along time and
+// keeps two solvers, so that the transfer of one chunk's data overlaps the
+// computation of the other's; the chunk chi^2 values are then added. Here the
+// two "solvers" are two device buffers: chunk i's data and weights are copied
+// on a second stream into buffer i mod 2 while the fused kernel reduces chunk
+// i - 1 on the context's stream. Events order the two streams:
+//   copied[b]  (copy stream)    -> the kernel of the chunk in buffer b may start;
+//   free[b]    (context stream) -> buffer b may be overwritten (two chunks on).
+// Each chunk's data are checked on arrival; each chunk's kernel writes its
+// chi^2 to its own slot, and one thread adds the slots in chunk order, so the
+// result does not depend on the chunking schedule's timing.
+#include "rime_internal.cuh"
+
+#include <algorithm>
+
+namespace rime {
+namespace {
+
+__global__ void k_sum_in_order(int n, const double *in, double *out, const DevStatus *st) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    if (inputs_bad(st)) return;
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += in[i];
+    *out = s;
+}
+
+// Grows the two chunk buffers to `bytes` each and the per-chunk results to
+// `nchunks`; creates the copy stream and events on first use.
+cudaError_t ensure(rime_ctx *c, size_t bytes, int nchunks) {
+    cudaError_t e;
+    if (!c->copy_stream) {
+        e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaEvent_t *evs[] = {&c->ev_start, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0], &c->ev_free[1]};
+        for (cudaEvent_t *ev : evs) {
+            e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    Alloc alloc{c};
+    if (bytes > c->sbuf_cap) {
+        for (int b = 0; b < 2; b++) {
+            if (c->d_sbuf[b]) cudaFree(c->d_sbuf[b]);
+            c->d_sbuf[b] = nullptr;
+        }
+        c->sbuf_cap = 0;
+        for (int b = 0; b < 2; b++) {
+            e = alloc(&c->d_sbuf[b], bytes);
+            if (e != cudaSuccess) return e;
+        }
+        c->sbuf_cap = bytes;
+    }
+    if ((size_t)nchunks > c->schi_cap) {
+        if (c->d_schi) cudaFree(c->d_schi);
+        c->d_schi = nullptr;
+        c->schi_cap = 0;
+        e = alloc((void **)&c->d_schi, (size_t)nchunks * sizeof(double));
+        if (e != cudaSuccess) return e;
+        c->schi_cap = nchunks;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rime
+
+using namespace rime;
+
+#define CKS(c, call, what)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail_ctx(c, e_, what);  \
+    } while (0)
+
+extern "C" {
+
+int32_t rime_stream_chunk_ntime(const rime_ctx *c) {
+    if (!c) return 0;
+    // about four waves of the fused kernel per chunk (2 blocks on each of the
+    // device's SMs per wave), so that each chunk's launch has little tail
+    int nsm = c->nsm;
+    if (nsm <= 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) nsm = 0;
+    if (nsm <= 0) nsm = 152;
+    long long per_t = narrow_applies(c) ? (long long)c->dims.nchan : (long long)c->dims.nchan * c->nunits;
+    long long nt = (4LL * 2 * nsm + per_t - 1) / std::max(1LL, per_t);
+    return (int32_t)std::max(1LL, std::min<long long>(nt, c->dims.ntime));
+}
+
+rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight, int32_t chunk_ntime,
+                               double *chi2) {
+    if (!c) return fail_ctx(nullptr, RIME_E_INVALID, "ctx is NULL");
+    if (!data) return fail_ctx(c, RIME_E_INVALID, "data is NULL");
+    if (!chi2) return fail_ctx(c, RIME_E_INVALID, "chi2 is NULL");
+    if (!c->sources_set) return fail_ctx(c, RIME_E_STATE, "rime_set_sources has not been called");
+    const int ntime = c->dims.ntime;
+    const int nt = chunk_ntime > 0 ? std::min<int>(chunk_ntime, ntime) : rime_stream_chunk_ntime(c);
+    const int nchunks = (ntime + nt - 1) / nt;
+    const size_t ts = c->tsize();
+    const size_t vis_t = (size_t)c->nbl * c->dims.nchan;           // visibilities per timestep
+    const size_t dbytes = vis_t * 8 * ts, wbytes = vis_t * ts;      // per timestep
+    CKS(c, ensure(c, (size_t)nt * std::max(dbytes + wbytes, (size_t)16), nchunks), "allocating chunk buffers");
+    CKS(c, reset_status_class(c, EC_SDATA), "reset status");
+    // the copy stream must not overwrite a buffer that earlier work on the
+    // context's stream still reads
+    CKS(c, cudaEventRecord(c->ev_start, c->stream), "event");
+    CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0), "stream wait");
+    const char *hd = static_cast<const char *>(data);
+    const char *hw = static_cast<const char *>(weight);
+    for (int i = 0; i < nchunks; i++) {
+        const int b = i & 1;
+        const int t0 = i * nt, nti = std::min(nt, ntime - t0);
+        char *bd = static_cast<char *>(c->d_sbuf[b]);
+        char *bw = bd + (size_t)nt * dbytes;
+        if (i >= 2) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0), "stream wait");
+        CKS(c, cudaMemcpyAsync(bd, hd + (size_t)t0 * dbytes, (size_t)nti * dbytes, cudaMemcpyDefault, c->copy_stream),
+            "copying a data chunk");
+        if (hw)
+            CKS(c, cudaMemcpyAsync(bw, hw + (size_t)t0 * wbytes, (size_t)nti * wbytes, cudaMemcpyDefault,
+                                   c->copy_stream),
+                "copying a weight chunk");
+        CKS(c, cudaEventRecord(c->ev_copied[b], c->copy_stream), "event");
+        CKS(c, cudaStreamWaitEvent(c->stream, c->ev_copied[b], 0), "stream wait");
+        CKS(c, launch_validate_chunk(c, (long long)nti * vis_t, bd, hw ? bw : nullptr, EC_SDATA,
+                                     (long long)t0 * vis_t),
+            "checking a chunk");
+        // the kernels index data and weights by the global timestep: hand them
+        // base addresses t0 rows before the chunk (never dereferenced there)
+        FusedParams P{};
+        fill_fused_params(c, P, nullptr, c->d_schi + i, nullptr, nullptr);
+        P.t_begin = t0;
+        P.data = reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(bd) - (uintptr_t)t0 * dbytes);
+        P.weight = hw ? reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(bw) - (uintptr_t)t0 * wbytes)
+                      : nullptr;
+        P.has_weight = hw != nullptr;
+        cudaError_t e = narrow_applies(c) ? launch_narrow_params(c, MODE_CHI2, P, nti)
+                                          : launch_tiled_params(c, MODE_CHI2, P,
+                                                                (long long)nti * c->dims.nchan * c->nunits);
+        CKS(c, e, "chunk chi2 kernel");
+        CKS(c, cudaEventRecord(c->ev_free[b], c->stream), "event");
+    }
+    k_sum_in_order<<<1, 32, 0, c->stream>>>(nchunks, c->d_schi, &c->d_status->chi2, c->d_status);
+    CKS(c, cudaGetLastError(), "chunk sum");
+    rime_status s = sync_status_ctx(c);
+    // streamed data errors belong to this call only
+    cudaError_t e = reset_status_class(c, EC_SDATA);
+    if (s != RIME_OK) return s;
+    CKS(c, e, "reset status");
+    *chi2 = c->h_status->chi2;
+    return RIME_OK;
+}
+
+}  // extern "C"
