@@ -262,7 +262,9 @@ typedef struct {
  * and gains: set j is sources src_offsets[j] .. src_offsets[j+1]-1 of `all`.
  * The paper evaluates one sky model per solve of its BIRO loop (Fig. 3,
  * Sec. 3); this entry point evaluates the many proposals of one sampler
- * iteration in one persistent launch (FP32) or one launch per set (FP64).
+ * iteration in one persistent launch of the tiled FP32 kernel, or in one
+ * launch per set (FP64, and arrays that the small-array kernel takes under
+ * rime_set_kernel: then the configuration below does not apply).
  *   nsets        >= 0 (0: nothing is computed)
  *   src_offsets  HOST array [nsets + 1], src_offsets[0] = 0, non-decreasing,
  *                src_offsets[nsets] = all->nsrc; empty sets are allowed

@@ -5,7 +5,7 @@
 // (t, channel group, antenna unit, group of sets), each the fused predict +
 // chi^2 of its sets' sources for the unit's baselines, then one fixed-order
 // sum per set.
-// FP64: one launch of the FP64 fused kernel per set.
+// FP64, and arrays the small-array kernel takes: one launch per set.
 //
 // The schedule (set order and source offsets) reaches the device as kernel
 // arguments, so a captured CUDA graph carries it and replays stand alone.
@@ -191,11 +191,13 @@ rime_status rime_chi2_batched(rime_ctx *c, int32_t nsets, const int32_t *off, co
     }
     if (!c->d_bcounter) CKB(c, alloc((void **)&c->d_bcounter, sizeof(unsigned long long)), "allocating a counter");
 
-    if (c->dims.precision == RIME_FP64) {
+    // one launch per set: FP64, and small arrays (whose tiled work items would
+    // be nearly empty blocks); each set's chi^2 is that of a plain call
+    if (c->dims.precision == RIME_FP64 || narrow_applies(c)) {
         for (int j = 0; j < nsets; j++)
             CKB(c, narrow_applies(c) ? launch_narrow(c, MODE_CHI2, nullptr, chi2_dev + j, off[j], off[j + 1])
                                      : launch_fused_f64_range(c, off[j], off[j + 1], chi2_dev + j),
-                "batched FP64 kernel");
+                "batched per-set kernel");
         return RIME_OK;
     }
 

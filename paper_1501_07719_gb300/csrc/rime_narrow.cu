@@ -157,13 +157,23 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
         offp[i] = (act[i] ? c : 0) * SC * na + p;
         offq[i] = (act[i] ? c : 0) * SC * na + q;
         offs[i] = (act[i] ? c : 0) * SC;
-        const double *xp = P.uvw + 3 * ((long long)t * na + p);
-        const double *xq = P.uvw + 3 * ((long long)t * na + q);
-        const double du = xp[0] - xq[0], dv = xp[1] - xq[1];
-        const double nu2 = (double)nu2_of(chan[kk[i]]);
-        du2[i] = (T)(nu2 * du * du);
-        dudv[i] = (T)(nu2 * du * dv);
-        dv2[i] = (T)(nu2 * dv * dv);
+        if constexpr (sizeof(T) == 4) {
+            // FP32 inputs are FP32 values: one rounding in the difference (the
+            // FP64 pipe runs at 1/64 of the FP32 rate; this setup is per pair)
+            const float4 xp = P.uvw_f[(long long)t * na + p], xq = P.uvw_f[(long long)t * na + q];
+            const float du = xp.x - xq.x, dv = xp.y - xq.y, nu2 = nu2_of(chan[kk[i]]);
+            du2[i] = nu2 * du * du;
+            dudv[i] = nu2 * du * dv;
+            dv2[i] = nu2 * dv * dv;
+        } else {
+            const double *xp = P.uvw + 3 * ((long long)t * na + p);
+            const double *xq = P.uvw + 3 * ((long long)t * na + q);
+            const double du = xp[0] - xq[0], dv = xp[1] - xq[1];
+            const double nu2 = nu2_of(chan[kk[i]]);
+            du2[i] = nu2 * du * du;
+            dudv[i] = nu2 * du * dv;
+            dv2[i] = nu2 * dv * dv;
+        }
     }
 
     T acc[M][8];

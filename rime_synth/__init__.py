@@ -78,6 +78,9 @@ WORKLOADS = {
                  npsrc=50, ngsrc=50, nsets=512, seed_index=3),
         Workload("256ant-20t-128ch-4096pt", na=256, ntime=20, nchan=128,
                  npsrc=4096, seed_index=4),
+        # Table 4's smallest array (KAT-7 shape) at the table's sizes
+        Workload("7ant-100t-64ch-50pt50g", na=7, ntime=100, nchan=64,
+                 npsrc=50, ngsrc=50, seed_index=207),
     )
 }
 

@@ -58,12 +58,22 @@ def _run(r, sets):
     return out.cpu().numpy()
 
 
+def _kernel(r, kernel):
+    """None: the library's choice (13 antennas: one small-array launch per
+    set); "tiled": the persistent launch of the tiled kernel (FP32)."""
+    import paper_1501_07719_gb300 as R
+    if kernel == "tiled":
+        r.set_kernel(R.RIME_KERNEL_TILED)
+
+
+@pytest.mark.parametrize("kernel", [None, "tiled"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("case", list(CASES))
-def test_batched_matches_oracle(case, precision):
+def test_batched_matches_oracle(case, precision, kernel):
     inp = _case(case, precision)
     sets = inp["sets"]
     r = gpu_ctx(inp, precision)
+    _kernel(r, kernel)
     got = _run(r, sets)
     r.close()
     for j in range(nsets(sets)):
@@ -71,27 +81,24 @@ def test_batched_matches_oracle(case, precision):
         assert rel_err(got[j], want) <= TOL[precision]["chi2"], (j, got[j], want)
 
 
+@pytest.mark.parametrize("kernel", [None, "tiled"])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-def test_batched_equals_plain_per_set(precision):
+def test_batched_equals_plain_per_set(precision, kernel):
     inp = _case("13ant", precision)
     sets = inp["sets"]
-    import paper_1501_07719_gb300 as R
     r = gpu_ctx(inp, precision)
+    _kernel(r, kernel)
     got = _run(r, sets)
     for j in range(nsets(sets)):
         r.set_sources(set_sources(sets, j))
-        auto = r.chi2()
-        if precision == "f64":
-            # the FP64 sets run one launch each of the kernel a plain call uses
-            assert got[j] == auto, j
+        plain = r.chi2()
+        if precision == "f64" or kernel is None:
+            # one launch per set of the kernel a plain call uses
+            assert got[j] == plain, j
         else:
-            # the batched FP32 launch runs the tiled kernel's per-item body: the
-            # same FP32 block sums as a plain tiled call, added in another order
-            r.set_kernel(R.RIME_KERNEL_TILED)
-            plain = r.chi2()
-            r.set_kernel(R.RIME_KERNEL_AUTO)
+            # the persistent FP32 launch runs the tiled kernel's per-item body:
+            # the same FP32 block sums as a plain tiled call, added in another order
             assert abs(got[j] - plain) <= 1e-12 * plain, j
-            assert rel_err(got[j], auto) <= TOL["f32"]["chi2"], j
     r.close()
 
 
@@ -99,6 +106,7 @@ def test_batched_configurations_agree_bitwise():
     inp = _case("13ant", "f32")
     sets = inp["sets"]
     r = gpu_ctx(inp, "f32")
+    _kernel(r, "tiled")   # the persistent launch, whose configuration this varies
     ref = _run(r, sets)
     for cpi in (1, 2, 4):
         for bps in (1, 2):
@@ -126,7 +134,8 @@ def test_tuner_picks_its_fastest_trial():
     assert all(t["ms"] > 0 for t in cfg["trials"])
 
 
-def test_batched_under_cuda_graph_replay():
+@pytest.mark.parametrize("kernel", [None, "tiled"])
+def test_batched_under_cuda_graph_replay(kernel):
     """Captured once; replays re-read the device source arrays updated in place."""
     import torch
     inp = _case("13ant", "f32")
@@ -140,6 +149,8 @@ def test_batched_under_cuda_graph_replay():
     import paper_1501_07719_gb300 as R
     rc = R.Rime(inp, R.RIME_FP32, data=inp["data"], weight=np.asarray(inp["weight"], np.float32), stream=s)
     rc.set_gains(inp["gains"])
+    _kernel(rc, kernel)
+    _kernel(r2, kernel)
     rc.chi2_batched(sets["offsets"], dev, out=out)   # first call: buffers and tuning
     rc.sync()
     g = torch.cuda.CUDAGraph()
