@@ -24,7 +24,7 @@ class _Problem(C.Structure):
     _fields_ = [
         ("na", C.c_int), ("ntime", C.c_int), ("nchan", C.c_int), ("nsrc", C.c_int),
         ("stokes_time_varying", C.c_int),
-        ("ref_freq_hz", C.c_double), ("beam_c", C.c_double),
+        ("ref_freq_hz", C.c_double), ("beam_c", C.c_double), ("beam_model", C.c_int),
         ("uvw", _dp), ("freq_hz", _dp), ("lm", _dp), ("stokes", _dp),
         ("alpha", _dp), ("shape", _dp), ("pointing", _dp), ("gains", _dp),
         ("data", _dp), ("weight", _dp),
@@ -70,7 +70,8 @@ def _ptr(a):
 class Problem:
     """Holds contiguous float64 copies of one problem's arrays.
 
-    inp: dict with na, ntime, nchan, ref_freq_hz, beam_c, uvw, freq,
+    inp: dict with na, ntime, nchan, ref_freq_hz, beam_c, beam_model
+         (optional: 0 cos^3, 1 Jinc), uvw, freq,
          pointing, sources{lm, stokes, alpha, shape}, gains, weight and
          optionally data (complex, [ntime][nbl][nchan][4]).
     """
@@ -94,7 +95,7 @@ class Problem:
         self.nbl = self.na * (self.na - 1) // 2
         self.s = _Problem(
             self.na, self.ntime, self.nchan, nsrc, tv,
-            float(inp["ref_freq_hz"]), float(inp["beam_c"]),
+            float(inp["ref_freq_hz"]), float(inp["beam_c"]), int(inp.get("beam_model", 0)),
             _ptr(k["uvw"]), _ptr(k["freq"]), _ptr(k["lm"]), _ptr(k["stokes"]),
             _ptr(k["alpha"]), _ptr(k["shape"]), _ptr(k["pointing"]),
             _ptr(k["gains"]), _ptr(k["data"]), _ptr(k["weight"]))

@@ -14,7 +14,10 @@
  *   Eq. 3   K_tps = exp(2 pi i (u l + v m + w (n - 1)) / lambda), n = sqrt(1-l^2-m^2)
  *   Eq. 4   E_ps = cos^3(C lambda |l_s - dl_p|), read as cos^3(C nu_GHz rho)
  *           with C in rad^-1 GHz^-1, the argument clamped at pi/2 (E = 0 past
- *           the first null)
+ *           the first null). Sec. 2.1 names a Jinc function for the VLA beam
+ *           in its place; beam_model 1 takes E = 2 J1(x) / x with the same
+ *           x = C nu_GHz rho (the Airy pattern of a uniformly illuminated
+ *           dish, unclamped: its sidelobes change sign).
  *   Eqs. 5-6 source coherency E_p K_p B K_q^H E_q^H, summed over sources
  *   Eq. 7   chi^2 = sum w (V - D)^2, read as w times the sum over the four
  *           correlations of |V_c - D_c|^2; the ln(2 pi / w) term separately.
@@ -30,6 +33,8 @@
  * Pinned by tests/test_oracle_pins.py (closed forms, invariants, an image-plane
  * quadrature of the Gaussian, a matrix formulation, finite differences).
  */
+/* j0 / j1 (Bessel functions of the first kind) are X/Open math functions */
+#define _XOPEN_SOURCE 700
 #include "rime_oracle.h"
 
 #include <complex.h>
@@ -114,6 +119,39 @@ typedef struct {
     cplx dK_dl, dK_dm;
 } antenna_term;
 
+/* The beam of eq. 4 as a function of x = C nu_GHz rho, and (dE/dx) / x.
+ *   model 0: E = cos^3 x for x < pi/2, 0 past it;
+ *            dE/dx = -3 cos^2 x sin x, so (dE/dx)/x = -3 cos^2 x (sin x / x).
+ *   model 1: E = 2 J1(x) / x; with J1' = J0 - J1/x, dE/dx = 2 (J0 - 2 J1/x) / x
+ *            = -2 J2(x) / x, so (dE/dx)/x = -2 (2 J1(x)/x - J0(x)) / x^2.
+ *            Near x = 0 the power series of 2 J1(x)/x,
+ *            sum_k (-1)^k (x/2)^(2k) / (k! (k+1)!) = 1 - x^2/8 + x^4/192 - ...,
+ *            and of its derivative over x, -1/4 + x^2/48 - x^4/1536 + ...,
+ *            avoid the cancellation of 2 J1/x - J0 (J0, J1: libm's j0, j1). */
+static void beam_factor(int model, double x, double *E, double *dEx) {
+    if (model == 1) {
+        if (x < 0.05) {
+            double x2 = x * x;
+            *E = 1.0 - x2 / 8.0 + x2 * x2 / 192.0 - x2 * x2 * x2 / 9216.0;
+            *dEx = -0.25 + x2 / 48.0 - x2 * x2 / 1536.0 + x2 * x2 * x2 / 92160.0;
+        } else {
+            double j1x = j1(x), j0x = j0(x);
+            *E = 2.0 * j1x / x;
+            *dEx = -2.0 * (2.0 * j1x / x - j0x) / (x * x);
+        }
+        return;
+    }
+    if (x >= PI / 2) {
+        *E = 0.0;
+        *dEx = 0.0;
+        return;
+    }
+    double c = cos(x);
+    double sinc = (x < 1e-8) ? 1.0 : sin(x) / x;
+    *E = c * c * c;
+    *dEx = -3.0 * c * c * sinc;
+}
+
 /* Eq. 3 and eq. 4 for antenna a, with the derivatives the gradient needs. */
 static antenna_term antenna_factor(const rime_oracle_problem *P, int t, int a,
                                    double l, double m, double nu, double lambda) {
@@ -135,19 +173,12 @@ static antenna_term antenna_factor(const rime_oracle_problem *P, int t, int a,
     double rho = hypot(l - dl, m - dm);
     double cnu = P->beam_c * (nu * 1e-9);
     double x = cnu * rho;
-    if (x >= PI / 2) {
-        r.E = 0.0;
-        r.dE_dl = r.dE_dm = 0.0;
-    } else {
-        double c = cos(x);
-        r.E = c * c * c;
-        /* dE/dl = -3 cos^2 x sin x * cnu * (l - dl) / rho
-         *       = -3 cos^2 x (sin x / x) cnu^2 (l - dl)   (finite at rho = 0) */
-        double sinc = (x < 1e-8) ? 1.0 : sin(x) / x;
-        double common = -3.0 * c * c * sinc * cnu * cnu;
-        r.dE_dl = common * (l - dl);
-        r.dE_dm = common * (m - dm);
-    }
+    double E, dEx;   /* E(x) and (dE/dx) / x */
+    beam_factor(P->beam_model, x, &E, &dEx);
+    r.E = E;
+    /* dE/dl = dE/dx * cnu * (l - dl) / rho = (dE/dx / x) cnu^2 (l - dl), finite at rho = 0 */
+    r.dE_dl = dEx * cnu * cnu * (l - dl);
+    r.dE_dm = dEx * cnu * cnu * (m - dm);
     return r;
 }
 

@@ -22,6 +22,7 @@ typedef struct {
     int stokes_time_varying;   /* 1: stokes is [ntime][nsrc][4] */
     double ref_freq_hz;        /* nu_ref of eq. 2 */
     double beam_c;             /* C of eq. 4, rad^-1 GHz^-1 */
+    int beam_model;            /* 0: cos^3 (eq. 4); 1: 2 J1(x)/x (Sec. 2.1's Jinc) */
     const double *uvw;         /* [ntime][na][3] metres */
     const double *freq_hz;     /* [nchan] */
     const double *lm;          /* [nsrc][2] radians */

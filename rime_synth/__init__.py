@@ -132,12 +132,15 @@ def draw_sources(rs: dict, n: int, gauss_mask) -> dict:
 
 
 def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = None,
-                pointing_sigma: float = 0.0, time_varying: bool = False, noise: bool = True) -> dict:
+                pointing_sigma: float = 0.0, time_varying: bool = False, noise: bool = True,
+                beam_model: int = 0, beam_c: float | None = None) -> dict:
     """All inputs of one workload except the observed data (see ``observe``).
 
     precision "f32" rounds every real input to float32 values. noise=False
     leaves the noise out (None; the other arrays are unchanged, every array
     has its own stream), for timing runs that do not need the data values.
+    beam_model: 0 the cos^3 beam of eq. 4, 1 the Jinc beam 2 J1(x)/x, with
+    x = beam_c nu_GHz rho (beam_c defaults to BEAM_C).
     """
     if isinstance(wl, str):
         wl = WORKLOADS[wl]
@@ -168,7 +171,8 @@ def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = N
     if pointing_sigma > 0.0:
         pointing = rs["pointing"].normal(0.0, pointing_sigma, size=(nt, na, 2))
     out = dict(workload=wl, precision=precision, na=na, ntime=nt, nchan=nc,
-               nbl=nbl, ref_freq_hz=REF_FREQ_HZ, beam_c=BEAM_C, uvw=uvw,
+               nbl=nbl, ref_freq_hz=REF_FREQ_HZ, beam_c=BEAM_C if beam_c is None else float(beam_c),
+               beam_model=int(beam_model), uvw=uvw,
                freq=freq, pointing=pointing, sources=src, gains=gains,
                noise=noise, weight=weight)
     if wl.nsets:

@@ -20,7 +20,12 @@ MUTANTS = [
     ("phase sign", "r.K = cos(phi) + IMAG * sin(phi);", "r.K = cos(phi) - IMAG * sin(phi);"),
     ("w term dropped", "uvw[2] * n1) / lambda", "uvw[2] * 0.0) / lambda"),
     ("n instead of n-1", "uvw[2] * n1) / lambda", "uvw[2] * (n1 + 1.0)) / lambda"),
-    ("beam squared not cubed", "r.E = c * c * c;", "r.E = c * c;"),
+    ("beam squared not cubed", "*E = c * c * c;", "*E = c * c;"),
+    ("jinc: J0 for 2 J1(x)/x", "*E = 2.0 * j1x / x;", "*E = j0x;"),
+    ("jinc: series x^2 term", "*E = 1.0 - x2 / 8.0 +", "*E = 1.0 - x2 / 4.0 +"),
+    ("grad: jinc derivative J2", "*dEx = -2.0 * (2.0 * j1x / x - j0x) / (x * x);",
+     "*dEx = -2.0 * (j1x / x - j0x) / (x * x);"),
+    ("grad: jinc derivative series", "*dEx = -0.25 + x2 / 48.0", "*dEx = -0.5 + x2 / 48.0"),
     ("beam in wavelength", "double cnu = P->beam_c * (nu * 1e-9);",
      "double cnu = P->beam_c * lambda;"),
     ("pointing sign", "hypot(l - dl, m - dm)", "hypot(l + dl, m - dm)"),
@@ -43,8 +48,7 @@ MUTANTS = [
      "return P->stokes + 4 * ((long)s * P->ntime + t);"),
     ("grad: phase derivative sign", "r.dK_dl = r.K * IMAG *", "r.dK_dl = r.K * (-IMAG) *"),
     ("grad: pa derivative sign", "- 2.0 * mn * mn * umin * umaj);", "+ 2.0 * mn * mn * umin * umaj);"),
-    ("grad: beam derivative factor", "double common = -3.0 * c * c * sinc * cnu * cnu;",
-     "double common = -3.0 * c * sinc * cnu * cnu;"),
+    ("grad: beam derivative factor", "*dEx = -3.0 * c * c * sinc;", "*dEx = -3.0 * c * sinc;"),
     ("grad: gain q imaginary sign", "for (int c = 0; c < 4; c++) dVi[c] = -IMAG * dVr[c];",
      "for (int c = 0; c < 4; c++) dVi[c] = IMAG * dVr[c];"),
     ("grad: alpha derivative", "* log(lambda_ref / lambda);", "* log(lambda / lambda_ref);"),

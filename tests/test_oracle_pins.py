@@ -114,6 +114,54 @@ def test_beam_null_clamp_and_pointing():
     np.testing.assert_allclose(V, [0.125, 0, 0, 0.125], rtol=1e-13)
 
 
+_J1_ZERO_1 = 3.8317059702075125   # first positive zero of J1 (Abramowitz & Stegun, Table 9.5)
+
+
+def _jinc_E(x):
+    """The Jinc beam from scipy's Bessel J1, independent of the oracle's libm."""
+    special = pytest.importorskip("scipy.special")
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x == 0, 1.0, 2 * special.j1(x) / np.where(x == 0, 1, x))
+
+
+def _beam_probe(x_q, beam_c=65.0, nu=1e9):
+    """V00 of a unit point source on one baseline with u = v = w = 0 (K = 1),
+    antenna p pointed at the source (E_p = 1): V00 = E(x_q), x = C nu_GHz rho."""
+    rho = x_q / (beam_c * nu * 1e-9)
+    inp = problem(uvw=np.zeros((1, 2, 3)), freq=[nu], lm=[[rho * 0.6, rho * 0.8]],
+                  stokes=[1.0, 0, 0, 0], ref_freq_hz=nu, beam_c=beam_c,
+                  pointing=np.array([[[rho * 0.6, rho * 0.8], [0.0, 0.0]]]))
+    inp["beam_model"] = 1
+    return vis_all(inp)[0, 0, 0]
+
+
+@pytest.mark.parametrize("x", [0.0, 1e-3, 0.0499, 0.0501, 0.7, 2.0, 3.3, 5.0, 7.0155867, 9.2])
+def test_beam_jinc_equals_bessel_definition(x):
+    """The Jinc beam that Sec. 2.1 names for the VLA, E = 2 J1(x)/x, against
+    scipy's J1: main lobe, both sides of the oracle's series/libm switch at
+    x = 0.05, the negative first sidelobe and the second (x near 7.0156, the
+    first zero of J2, is its extremum)."""
+    V = _beam_probe(x)
+    want = float(_jinc_E(x))
+    np.testing.assert_allclose(V, [want, 0, 0, want], rtol=1e-14, atol=1e-16)
+
+
+def test_beam_jinc_nulls_and_both_antennas():
+    """E vanishes at the first zero of J1; with neither antenna pointed at the
+    source V00 = E(x_p) E(x_q), which is negative when one of them sees the
+    source in a sidelobe."""
+    assert abs(_beam_probe(_J1_ZERO_1)[0]) < 1e-15
+    nu, beam_c = 1.4e9, 65.0
+    cnu = beam_c * nu * 1e-9
+    l = 4.5 / cnu
+    inp = problem(uvw=np.zeros((1, 2, 3)), freq=[nu], lm=[[l, 0.0]], stokes=[1.0, 0, 0, 0], ref_freq_hz=nu,
+                  beam_c=beam_c, pointing=np.array([[[3.0 / cnu, 0.0], [0.0, 0.0]]]))
+    inp["beam_model"] = 1
+    V00 = vis_all(inp)[0, 0, 0, 0]
+    want = _jinc_E(1.5) * _jinc_E(4.5)
+    assert want < 0 and V00 == pytest.approx(want, rel=1e-14)
+
+
 # --------------------------------------------------------------------------
 # Gaussian shape: Fourier transform of the image-plane Gaussian, by quadrature
 # --------------------------------------------------------------------------
@@ -348,17 +396,21 @@ def _get_param(inp, s, j):
     return src["shape"][s, j - 7]
 
 
-def _fd_problem():
+def _fd_problem(beam_model=0):
     inp = _random_small(seed=5, na=4, ntime=2, nchan=3, npsrc=1, ngsrc=2, pointing=0.004)
     # larger offsets so the beam derivative matters; data = model + noise
     inp["sources"]["lm"] *= 0.8
+    if beam_model == 1:
+        # the Jinc beam with x = C nu rho reaching its first sidelobe
+        inp["beam_model"], inp["beam_c"] = 1, 400.0
     V = vis_all(inp)
     inp["data"] = V + inp["noise"] * 30
     return inp
 
 
-def test_gradient_matches_central_differences_sources():
-    inp = _fd_problem()
+@pytest.mark.parametrize("beam_model", [0, 1])
+def test_gradient_matches_central_differences_sources(beam_model):
+    inp = _fd_problem(beam_model)
     chi, gs, _ = oracle.Problem(inp).chi2_grad(want_gains=False)
     assert chi == pytest.approx(oracle.Problem(inp).chi2(), rel=1e-13)
     nsrc = gs.shape[0]
@@ -376,8 +428,28 @@ def test_gradient_matches_central_differences_sources():
     assert np.all(gs[0, 7:] == 0.0)
 
 
-def test_gradient_matches_central_differences_gains():
-    inp = _fd_problem()
+def test_gradient_jinc_beam_near_its_centre():
+    """The Jinc beam's derivative on its power-series branch (x < 0.05): a
+    source 1e-4 rad from the pointing centre, central differences in l, m."""
+    inp = _random_small(seed=9, na=3, ntime=1, nchan=2, npsrc=1, ngsrc=0, pointing=0.0)
+    inp["sources"]["lm"][:] = [[1e-4, -2e-4]]
+    inp["uvw"][:] = 0.0      # K = 1: chi^2 depends on (l, m) through the beam alone
+    inp["beam_model"] = 1
+    inp["data"] = vis_all(inp) + inp["noise"] * 30
+    _, gs, _ = oracle.Problem(inp).chi2_grad(want_gains=False)
+    cnu = inp["beam_c"] * inp["freq"].max() * 1e-9
+    assert cnu * np.hypot(1e-4, 2e-4) < 0.05
+    for j in (0, 1):
+        x0 = _get_param(inp, 0, j)
+        h = 1e-6   # chi^2 is smooth here; a smaller step drowns the difference in rounding
+        fd = (oracle.Problem(_set_param(inp, 0, j, x0 + h)).chi2()
+              - oracle.Problem(_set_param(inp, 0, j, x0 - h)).chi2()) / (2 * h)
+        assert abs(gs[0, j] - fd) < 1e-6 * abs(fd), (j, gs[0, j], fd)
+
+
+@pytest.mark.parametrize("beam_model", [0, 1])
+def test_gradient_matches_central_differences_gains(beam_model):
+    inp = _fd_problem(beam_model)
     _, _, gg = oracle.Problem(inp).chi2_grad(want_gains=True)
     rng = np.random.default_rng(3)
     picks = [(rng.integers(2), rng.integers(4), rng.integers(3), rng.integers(4))
