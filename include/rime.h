@@ -221,6 +221,22 @@ rime_status rime_chi2_streamed(rime_ctx *ctx, const void *data, const void *weig
  * kernel per chunk, at most ntime. 0 for a NULL context. */
 int32_t rime_stream_chunk_ntime(const rime_ctx *ctx);
 
+/* Primary beam models E(x), x = beam_c * nu[GHz] * rho, rho the distance of
+ * the source from the antenna's pointing centre (rime_set_beam). */
+typedef enum {
+    RIME_BEAM_COS3 = 0,   /* eq. 4 (WSRT): cos^3 x for x < pi/2, zero past the first null (default) */
+    RIME_BEAM_JINC = 1    /* the Jinc that Sec. 2.1 names for the VLA: 2 J1(x) / x, the Airy
+                             pattern of a uniformly illuminated dish (sidelobes change sign) */
+} rime_beam;
+
+/* Selects the beam model and its constant C (rad^-1 GHz^-1: 65 for the WSRT
+ * cos^3 beam; pi D / (c * 1e-9 s) ~ 262 for a 25 m dish's Jinc). Applies to
+ * every later call of the context (predict, chi^2, gradient, batched,
+ * streamed, tensor-core modes). Does not wait.
+ *   model   a rime_beam; RIME_E_INVALID otherwise
+ *   beam_c  finite, >= 0; RIME_E_INVALID otherwise */
+rime_status rime_set_beam(rime_ctx *ctx, int32_t model, double beam_c);
+
 /* Direct-sum kernels of rime_predict, rime_chi2 and rime_chi2_async
  * (rime_set_kernel). */
 typedef enum {

@@ -18,6 +18,7 @@ RIME_OK, RIME_E_INVALID, RIME_E_STATE, RIME_E_OOM, RIME_E_CUDA, RIME_E_TIMEOUT, 
 RIME_FP32, RIME_FP64 = 0, 1
 RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 = 0, 1, 2
 RIME_KERNEL_AUTO, RIME_KERNEL_TILED, RIME_KERNEL_NARROW = 0, 1, 2
+RIME_BEAM_COS3, RIME_BEAM_JINC = 0, 1
 
 
 class rime_dims(C.Structure):
@@ -77,10 +78,11 @@ def lib():
         L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
         L.rime_set_kernel.argtypes = [vp, C.c_int32]
+        L.rime_set_beam.argtypes = [vp, C.c_int32, C.c_double]
         L.rime_chi2_streamed.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
         L.rime_stream_chunk_ntime.argtypes, L.rime_stream_chunk_ntime.restype = [vp], C.c_int32
         for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
-                  "rime_set_kernel", "rime_chi2_streamed"):
+                  "rime_set_kernel", "rime_chi2_streamed", "rime_set_beam"):
             getattr(L, f).restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
@@ -305,6 +307,11 @@ def rime_chi2_streamed(ctx, precision, data, weight=None, chunk_ntime: int = 0) 
 
 def rime_stream_chunk_ntime(ctx) -> int:
     return int(lib().rime_stream_chunk_ntime(ctx))
+
+
+def rime_set_beam(ctx, model: int, beam_c: float):
+    """RIME_BEAM_COS3 (eq. 4) or RIME_BEAM_JINC, with the constant C (rad^-1 GHz^-1)."""
+    _check(lib().rime_set_beam(ctx, int(model), float(beam_c)), ctx)
 
 
 def rime_set_kernel(ctx, kernel: int):

@@ -28,6 +28,8 @@ class Rime:
         self.ctx = A.rime_create(self.na, self.ntime, self.nchan, precision, obs["freq"], obs["uvw"],
                                  obs.get("pointing"), data, weight, self.stream.cuda_stream,
                                  float(obs["ref_freq_hz"]), float(obs["beam_c"]))
+        if int(obs.get("beam_model", 0)) != A.RIME_BEAM_COS3:
+            self.set_beam(int(obs["beam_model"]), float(obs["beam_c"]))
 
     # inputs ---------------------------------------------------------------
     def set_uvw(self, uvw, pointing=None):
@@ -95,6 +97,11 @@ class Rime:
         """Tensor-core split-precision source sum for point sources
         (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32) or the direct sum (RIME_TC_OFF)."""
         A.rime_set_tensor_mode(self.ctx, mode)
+
+    def set_beam(self, model: int, beam_c: float):
+        """Beam model of eq. 4's E: RIME_BEAM_COS3 (default) or RIME_BEAM_JINC,
+        with its constant C in rad^-1 GHz^-1."""
+        A.rime_set_beam(self.ctx, model, beam_c)
 
     def set_kernel(self, kernel: int):
         """Direct-sum kernel: RIME_KERNEL_AUTO (default), RIME_KERNEL_TILED or

@@ -413,6 +413,17 @@ rime_status rime_set_tensor_mode(rime_ctx *c, int32_t mode) {
     return RIME_OK;
 }
 
+rime_status rime_set_beam(rime_ctx *c, int32_t model, double beam_c) {
+    if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
+    if (model != RIME_BEAM_COS3 && model != RIME_BEAM_JINC)
+        return fail(c, RIME_E_INVALID, "model must be RIME_BEAM_COS3 or RIME_BEAM_JINC");
+    if (!(beam_c >= 0.0) || !std::isfinite(beam_c)) return fail(c, RIME_E_INVALID, "beam_c must be finite and >= 0");
+    c->beam_model = model;
+    c->dims.beam_c = beam_c;
+    CK(c, launch_prep_channels(c), "channel constants");
+    return RIME_OK;
+}
+
 rime_status rime_set_kernel(rime_ctx *c, int32_t kernel) {
     if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
     if (kernel != RIME_KERNEL_AUTO && kernel != RIME_KERNEL_TILED && kernel != RIME_KERNEL_NARROW)

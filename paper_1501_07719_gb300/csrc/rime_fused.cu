@@ -108,9 +108,7 @@ __device__ __forceinline__ double2 antenna_factor(double tau, double rho, double
     double r = ph - round_int_d(ph);
     double sn, cs;
     sincospi(2.0 * r, &sn, &cs);
-    double x = ch.cnu * rho;                 // eq. 4: C nu[GHz] rho
-    double cb = cos(x);
-    double E = (x < 1.5707963267948966) ? cb * cb * cb : 0.0;
+    double E = beam_E(ch.beam, ch.cnu * rho);   // eq. 4 at C nu[GHz] rho
     double amp = E * exp2(alpha * ch.hlr);   // sqrt of eq. 2's spectral factor
     return make_double2(amp * cs, amp * sn);
 }
@@ -413,8 +411,11 @@ __device__ __forceinline__ float2 gauss2(float2 qp, float2 up, float2 vp, float2
 }
 
 // One work item: timestep t, channel k, antenna unit u, sources [sb, se).
-// Returns the block's chi^2 (in thread 0; chi^2 modes only).
-template <int MODE>
+// Returns the block's chi^2 (in thread 0; chi^2 modes only). JINC selects the
+// beam model at compile time: this kernel runs at its register limit, and a
+// run-time choice (the Bessel function's code beside cos^3 in the staging
+// loop) cost it 1.5 %.
+template <int MODE, bool JINC>
 __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se) {
     constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     const int tid = threadIdx.x;
@@ -503,7 +504,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         for (int s = it_s0, a = it_a0; s < sc;) {
             float2 v = phase_factor(S.rTau[s * NLOC + a], ch);
             if (pointing) {
-                float E = beam(S.rRho[s * NLOC + a], ch);
+                float E = beam_E(JINC ? RIME_BEAM_JINC : RIME_BEAM_COS3, ch.cnu * S.rRho[s * NLOC + a]);
                 v.x *= E;
                 v.y *= E;
             }
@@ -528,7 +529,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             // spectral factor (nu / nu_ref)^alpha = 2^(2 alpha hlr) of eq. 2
             float f = exp2f(2.0f * S.rAl[tid] * ch.hlr);
             if (!pointing) {
-                float E = beam(S.rRho[tid * NLOC], ch);
+                float E = beam_E(JINC ? RIME_BEAM_JINC : RIME_BEAM_COS3, ch.cnu * S.rRho[tid * NLOC]);
                 f *= E * E;
             }
             float4 st = S.rSt[tid];
@@ -720,7 +721,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     return bsum;
 }
 
-template <int MODE>
+template <int MODE, bool JINC>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -730,7 +731,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
     const int t = P.t_begin + rest / P.nchan;
-    const double bsum = fused_item<MODE>(P, S, t, k, u, 0, P.nsrc);
+    const double bsum = fused_item<MODE, JINC>(P, S, t, k, u, 0, P.nsrc);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
 }
 
@@ -741,6 +742,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
 // item share their data, weights and gains, which the later sets read from
 // L1. One partial per (set, t, channel, unit): the sums do not depend on the
 // schedule.
+template <bool JINC>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(const FusedParams P, const BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(co
         for (int rank = g * B.gsets; rank < r1; rank++) {
             const int j = B.order[rank];
             for (int k = kc * B.cpi; k < k1; k++) {
-                const double bsum = fused_item<MODE_CHI2>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
+                const double bsum = fused_item<MODE_CHI2, JINC>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
                 if (threadIdx.x == 0)
                     B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
                 __syncthreads();
@@ -948,10 +950,15 @@ cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, lon
         }
     }
     size_t sm = sizeof(f32::Smem);
+    if (c->beam_model == RIME_BEAM_JINC) switch (mode) {
+            case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, true>, P, blocks, f32::THREADS, sm, c->stream);
+            case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, true>, P, blocks, f32::THREADS, sm, c->stream);
+            default: return launch_k(f32::k_fused_f32<MODE_GRAD, true>, P, blocks, f32::THREADS, sm, c->stream);
+        }
     switch (mode) {
-        case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT>, P, blocks, f32::THREADS, sm, c->stream);
-        case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2>, P, blocks, f32::THREADS, sm, c->stream);
-        default: return launch_k(f32::k_fused_f32<MODE_GRAD>, P, blocks, f32::THREADS, sm, c->stream);
+        case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, false>, P, blocks, f32::THREADS, sm, c->stream);
+        case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, false>, P, blocks, f32::THREADS, sm, c->stream);
+        default: return launch_k(f32::k_fused_f32<MODE_GRAD, false>, P, blocks, f32::THREADS, sm, c->stream);
     }
 }
 
@@ -960,19 +967,21 @@ cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid) {
     fill_fused_params(c, P, nullptr, nullptr, nullptr, nullptr);
     if (grid <= 0 || B.nitems == 0) return cudaSuccess;
     const size_t sm = sizeof(f32::Smem);
-    cudaError_t e = cudaFuncSetAttribute(f32::k_batched_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto kern = c->beam_model == RIME_BEAM_JINC ? f32::k_batched_f32<true> : f32::k_batched_f32<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    f32::k_batched_f32<<<grid, f32::THREADS, sm, c->stream>>>(P, B);
+    kern<<<grid, f32::THREADS, sm, c->stream>>>(P, B);
     return cudaGetLastError();
 }
 
 int batched_blocks_per_sm() {
+    // both beam instances take the same registers and shared memory
     int n = 0;
-    if (cudaFuncSetAttribute(f32::k_batched_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(f32::k_batched_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(f32::Smem)) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32::k_batched_f32, f32::THREADS, sizeof(f32::Smem)) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f32::k_batched_f32<false>, f32::THREADS,
+                                                      sizeof(f32::Smem)) != cudaSuccess)
         return 0;
     return n;
 }

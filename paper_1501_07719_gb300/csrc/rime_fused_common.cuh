@@ -5,6 +5,7 @@
 #pragma once
 #include "rime_internal.cuh"
 #include "rime_dev.cuh"
+#include "rime_beam.cuh"
 
 namespace rime {
 
@@ -71,12 +72,8 @@ __device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
     return make_float2(cs, sn);
 }
 
-// Beam E = cos^3(C nu[GHz] rho) (eq. 4), zero past the first null.
-__device__ __forceinline__ float beam(float rho, const ChanF &ch) {
-    float x = ch.cnu * rho;
-    float cb = cosf(x);
-    return (x < 1.57079632679f) ? cb * cb * cb : 0.0f;
-}
+// Beam E of eq. 4 (or the Jinc model) at x = C nu[GHz] rho.
+__device__ __forceinline__ float beam(float rho, const ChanF &ch) { return beam_E(ch.beam, ch.cnu * rho); }
 
 }  // namespace f32
 

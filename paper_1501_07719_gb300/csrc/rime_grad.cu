@@ -19,6 +19,7 @@
 // per (t, channel group, unit) and source is written and k_colsum sums them
 // in a fixed order.
 #include "rime_internal.cuh"
+#include "rime_beam.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -112,34 +113,6 @@ template <typename T>
 __device__ __forceinline__ T nu_of(const typename GCfg<T>::Chan &ch);
 template <> __device__ __forceinline__ float nu_of<float>(const ChanF &ch) { return ch.nu_hi + ch.nu_lo; }
 template <> __device__ __forceinline__ double nu_of<double>(const ChanD &ch) { return ch.nu; }
-
-// Beam E = cos^3(x), x = C nu rho (eq. 4), and dlnE/dx-related factor:
-// returns E and t3 = -3 tan(x) / x (so dlnE/dl = t3 cnu^2 (l - dl)); both 0
-// past the first null.
-template <typename T>
-__device__ __forceinline__ void beam_d(T cnu, T rho, T &E, T &t3) {
-    T x = cnu * rho;
-    if (x >= T(1.5707963267948966)) {
-        E = 0;
-        t3 = 0;
-        return;
-    }
-    T sn, cs;
-    if (sizeof(T) == 4) {
-        float s_, c_;
-        sincosf((float)x, &s_, &c_);
-        sn = s_;
-        cs = c_;
-    } else {
-        double s_, c_;
-        sincos((double)x, &s_, &c_);
-        sn = (T)s_;
-        cs = (T)c_;
-    }
-    E = cs * cs * cs;
-    T tx = (x < T(1e-4)) ? T(1) + x * x / T(3) : sn / (cs * x);   // tan(x) / x
-    t3 = T(-3) * tx;
-}
 
 template <typename T>
 struct GSmem {
@@ -274,7 +247,7 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
                 const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
                 const T *ex = reinterpret_cast<const T *>(P.extra) + 8 * src;
                 T E, t3;
-                beam_d<T>(ch.cnu, rRho[i], E, t3);
+                beam_Ed(ch.beam, ch.cnu * rRho[i], E, t3);
                 v.x *= E;
                 v.y *= E;
                 T2 d;   // dlnE/dl, dlnE/dm = t3 cnu^2 (l - dl_ta, m - dm_ta)  (eq. 4)
@@ -339,7 +312,7 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
         T dlnE2_l = 0, dlnE2_m = 0;
         if (!pointing) {
             T E, t3;                            // the beam E_s^2 shared by both antennas
-            beam_d<T>(ch.cnu, rRho[sl], E, t3);
+            beam_Ed(ch.beam, ch.cnu * rRho[sl], E, t3);
             w *= E * E;
             const T cnu2 = ch.cnu * ch.cnu;
             dlnE2_l = T(2) * t3 * cnu2 * (T)l;
@@ -497,7 +470,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
                 const T *exq = reinterpret_cast<const T *>(P.extra) + 8 * src;
                 T E, t3;
-                beam_d<T>(ch.cnu, rRho[i], E, t3);
+                beam_Ed(ch.beam, ch.cnu * rRho[i], E, t3);
                 v.x *= E;
                 v.y *= E;
                 T2 d;
@@ -584,7 +557,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
             T dlnE2_l = 0, dlnE2_m = 0;
             if (!pointing) {
                 T E, t3;
-                beam_d<T>(ch.cnu, rRho[2 * sp + h], E, t3);
+                beam_Ed(ch.beam, ch.cnu * rRho[2 * sp + h], E, t3);
                 w *= E * E;
                 const T cnu2 = ch.cnu * ch.cnu;
                 dlnE2_l = T(2) * t3 * cnu2 * l;

@@ -80,11 +80,13 @@ struct ChanF {
     float hlr;            // 0.5 log2(nu / nu_ref): sqrt of the spectral factor is 2^(alpha hlr)
     float cnu;            // beam_c * nu[GHz]
     float nu2;            // nu^2 (Hz^2), for the Gaussian exponent
-    float pad[3];
+    int beam;             // rime_beam model of eq. 4's E (argument cnu * rho)
+    float pad[2];
 };
 // Per-channel constants, double precision path.
 struct ChanD {
     double nu, hlr, cnu, nu2;
+    int beam, pad;        // rime_beam model of eq. 4's E (argument cnu * rho)
 };
 
 struct rime_ctx_impl;  // forward
@@ -218,6 +220,7 @@ struct rime_ctx {
     // tensor-core split-precision mode (FP32 contexts)
     int tc_mode = 0;                  // rime_tc_mode
     int kernel = 0;                   // rime_kernel
+    int beam_model = 0;               // rime_beam
     // streamed chi^2 (rime_stream.cu): a copy stream, two chunk buffers
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};

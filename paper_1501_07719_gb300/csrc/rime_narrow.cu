@@ -92,13 +92,9 @@ __device__ __forceinline__ double2 phase_of(const double *tau, long long di, con
     sincospi(2.0 * r, &sn, &cs);
     return make_double2(cs, sn);
 }
-// E = cos^3(C nu[GHz] rho), zero past the first null (eq. 4).
+// E of eq. 4 (or the Jinc model) at C nu[GHz] rho.
 __device__ __forceinline__ float beam_of(float rho, const ChanF &ch) { return f32::beam(rho, ch); }
-__device__ __forceinline__ double beam_of(double rho, const ChanD &ch) {
-    const double x = ch.cnu * rho;
-    const double cb = cos(x);
-    return (x < 1.5707963267948966) ? cb * cb * cb : 0.0;
-}
+__device__ __forceinline__ double beam_of(double rho, const ChanD &ch) { return beam_E(ch.beam, ch.cnu * rho); }
 // (nu / nu_ref)^alpha = 2^(2 alpha hlr)
 __device__ __forceinline__ float spectral(float alpha, const ChanF &ch) { return exp2f(2.0f * alpha * ch.hlr); }
 __device__ __forceinline__ double spectral(double alpha, const ChanD &ch) { return exp2(2.0 * alpha * ch.hlr); }

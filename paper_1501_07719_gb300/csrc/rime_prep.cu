@@ -21,7 +21,7 @@ __device__ __forceinline__ void flag(DevStatus *st, int cls, int bits, long long
 __device__ __forceinline__ bool finite(double x) { return isfinite(x); }
 
 // Per-channel constants of eqs. 2-4.
-__global__ void k_prep_channels(int nchan, const double *freq, double ref_freq, double beam_c,
+__global__ void k_prep_channels(int nchan, const double *freq, double ref_freq, double beam_c, int beam_model,
                                 int fp64, void *chan, DevStatus *st) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nchan) return;
@@ -32,7 +32,7 @@ __global__ void k_prep_channels(int nchan, const double *freq, double ref_freq, 
     double hlr = 0.5 * log2(nu / ref_freq);
     double cnu = beam_c * (nu * 1e-9);
     if (fp64) {
-        ChanD c{nu, hlr, cnu, nu * nu};
+        ChanD c{nu, hlr, cnu, nu * nu, beam_model, 0};
         reinterpret_cast<ChanD *>(chan)[k] = c;
     } else {
         ChanF c;
@@ -41,7 +41,8 @@ __global__ void k_prep_channels(int nchan, const double *freq, double ref_freq, 
         c.hlr = (float)hlr;
         c.cnu = (float)cnu;
         c.nu2 = (float)(nu * nu);
-        c.pad[0] = c.pad[1] = c.pad[2] = 0.f;
+        c.beam = beam_model;
+        c.pad[0] = c.pad[1] = 0.f;
         reinterpret_cast<ChanF *>(chan)[k] = c;
     }
 }
@@ -203,7 +204,7 @@ inline unsigned blocks_for(long long n) { return (unsigned)((n + kThreads - 1) /
 cudaError_t launch_prep_channels(rime_ctx *c) {
     int n = c->dims.nchan;
     k_prep_channels<<<blocks_for(n), kThreads, 0, c->stream>>>(
-        n, c->d_freq, c->dims.ref_freq_hz, c->dims.beam_c, c->dims.precision == RIME_FP64, c->d_chan,
+        n, c->d_freq, c->dims.ref_freq_hz, c->dims.beam_c, c->beam_model, c->dims.precision == RIME_FP64, c->d_chan,
         c->d_status);
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@
 #include "rime_internal.cuh"
 #include "rime_dev.cuh"
 #include "rime_tc.cuh"
+#include "rime_beam.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -108,11 +109,7 @@ __device__ __forceinline__ float2 phase_sfu(float2 tau, const ChanF &ch) {
     __sincosf(6.28318530717958648f * f, &sn, &cs);
     return make_float2(cs, sn);
 }
-__device__ __forceinline__ float beam_f(float rho, const ChanF &ch) {
-    const float x = ch.cnu * rho;
-    const float cb = cosf(x);
-    return x < 1.57079632679f ? cb * cb * cb : 0.f;
-}
+__device__ __forceinline__ float beam_f(float rho, const ChanF &ch) { return beam_E(ch.beam, ch.cnu * rho); }
 
 // (x, y) -> packed hi and lo words: BF16 pairs (x in the low half).
 __device__ __forceinline__ uint32_t pack_bf16(float x, float y) {

@@ -10,10 +10,17 @@ import rime_synth
 TOL = {"f64": dict(vis=1e-12, chi2=1e-10), "f32": dict(vis=1e-4, chi2=1e-4)}
 
 
+# the Jinc beam (beam_model 1) with the constant of a 25 m dish, so that the
+# seeded sources (|l|, |m| < 0.01) fall in its main lobe, first null and
+# first (negative) sidelobe
+JINC = dict(beam_model=1, beam_c=262.0)
+
+
 def make_case(wl, precision="f64", pointing_sigma=0.0, time_varying=False, seed=None,
-              gains=True, unit_weights=None):
+              gains=True, unit_weights=None, beam_model=0, beam_c=None):
     inp = rime_synth.make_inputs(wl, precision=precision, seed=seed,
-                                 pointing_sigma=pointing_sigma, time_varying=time_varying)
+                                 pointing_sigma=pointing_sigma, time_varying=time_varying,
+                                 beam_model=beam_model, beam_c=beam_c)
     if not gains:
         inp["gains"] = None
     if unit_weights:

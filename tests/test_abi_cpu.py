@@ -79,6 +79,7 @@ def test_null_context_calls_are_rejected(L):
     assert L.rime_batched_config(None, None) == 1
     assert L.rime_set_batched_config(None, None) == 1
     assert L.rime_set_kernel(None, 0) == 1
+    assert L.rime_set_beam(None, 0, 65.0) == 1
     assert L.rime_chi2_streamed(None, None, None, 0, None) == 1
     assert L.rime_stream_chunk_ntime(None) == 0
     assert L.rime_set_tensor_mode(None, 0) == 1

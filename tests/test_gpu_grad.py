@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import rime_synth
-from gpu_cases import gpu_ctx, make_case, rel_err
+from gpu_cases import JINC, gpu_ctx, make_case, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,9 @@ CASES = {
     "70ant-units": dict(wl=rime_synth.custom(70, 2, 3, 6, 5, seed_index=52)),
     "10ant-pointing": dict(wl=rime_synth.custom(10, 2, 4, 5, 5, seed_index=53), pointing_sigma=0.004),
     "9ant-no-gains": dict(wl=rime_synth.custom(9, 2, 3, 4, 4, seed_index=54), gains=False),
+    # the Jinc beam's derivative, per antenna and folded
+    "10ant-jinc-pointing": dict(wl=rime_synth.custom(10, 2, 4, 5, 5, seed_index=58), pointing_sigma=0.004, **JINC),
+    "12ant-jinc": dict(wl=rime_synth.custom(12, 2, 3, 6, 4, seed_index=59), **JINC),
 }
 
 
@@ -50,11 +53,15 @@ def _check(got, want, tol, what):
 def test_gradient_matches_oracle(case, precision):
     inp = _scaled_case(case, precision)
     chi_ref, gs_ref, gg_ref = oracle.Problem(inp, data=inp["data"]).chi2_grad(want_gains=True)
+    import paper_1501_07719_gb300 as R
     r = gpu_ctx(inp, precision)
     chi, gs, gg = r.chi2_grad(want_gains=True)
+    chi_auto = r.chi2()
+    r.set_kernel(R.RIME_KERNEL_TILED)   # the gradient's forward pass is the tiled kernel
     chi_plain = r.chi2()
     r.close()
     assert chi == chi_plain
+    assert rel_err(chi, chi_auto) <= (1e-12 if precision == "f64" else 1e-5)
     assert rel_err(chi, chi_ref) <= (1e-10 if precision == "f64" else 1e-4)
     gs = gs.cpu().numpy()
     gg = gg.cpu().numpy().reshape(gg_ref.shape)

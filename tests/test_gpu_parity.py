@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import rime_synth
-from gpu_cases import TOL, gpu_ctx, gpu_run, make_case, oracle_chi2, rel_err, vis_err
+from gpu_cases import JINC, TOL, gpu_ctx, gpu_run, make_case, oracle_chi2, rel_err, vis_err
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +40,12 @@ CASES = {
     "32ant": dict(wl=rime_synth.custom(32, 1, 2, 3, 3, seed_index=33), pointing_sigma=0.001),
     # 33..45 antennas: 512-thread blocks of two pairs each (45: the largest)
     "45ant-max": dict(wl=rime_synth.custom(45, 2, 2, 17, 5, seed_index=35), pointing_sigma=0.001),
+    # the Jinc beam model: per-antenna (pointing errors) and folded into the
+    # Stokes scale (none), across units and both kernels
+    "13ant-jinc-pointing": dict(wl=rime_synth.custom(13, 3, 5, 20, 17, seed_index=36), pointing_sigma=0.003,
+                                **JINC),
+    "70ant-jinc": dict(wl=rime_synth.custom(70, 2, 3, 6, 5, seed_index=37), **JINC),
+    "20ant-jinc": dict(wl=rime_synth.custom(20, 2, 3, 9, 9, seed_index=38), **JINC),
 }
 
 

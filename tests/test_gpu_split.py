@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import rime_synth
-from gpu_cases import gpu_ctx, make_case, rel_err, vis_err
+from gpu_cases import JINC, gpu_ctx, make_case, rel_err, vis_err
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,9 @@ CASES = {
     "9ant-1src": dict(wl=rime_synth.custom(9, 2, 1, 1, 0, seed_index=73), gains=False, unit_weights=True),
     # time-varying brightness
     "20ant-tv": dict(wl=rime_synth.custom(20, 3, 2, 12, 0, seed_index=74), time_varying=True),
+    # the Jinc beam: folded into the Stokes scales, and per antenna
+    "13ant-jinc": dict(wl=rime_synth.custom(13, 2, 3, 37, 0, seed_index=80), **JINC),
+    "130ant-jinc-pointing": dict(wl=rime_synth.custom(130, 1, 2, 20, 0, seed_index=81), pointing_sigma=0.004, **JINC),
 }
 
 
