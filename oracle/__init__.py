@@ -26,7 +26,7 @@ class _Problem(C.Structure):
         ("stokes_time_varying", C.c_int),
         ("ref_freq_hz", C.c_double), ("beam_c", C.c_double), ("beam_model", C.c_int),
         ("uvw", _dp), ("freq_hz", _dp), ("lm", _dp), ("stokes", _dp),
-        ("alpha", _dp), ("shape", _dp), ("pointing", _dp), ("gains", _dp),
+        ("alpha", _dp), ("shape", _dp), ("kind", _ip), ("pointing", _dp), ("gains", _dp),
         ("data", _dp), ("weight", _dp),
     ]
 
@@ -83,6 +83,7 @@ class Problem:
             "lm": _f64(src["lm"]), "stokes": _f64(src["stokes"]),
             "alpha": _f64(src["alpha"]),
             "shape": _f64(src.get("shape")),
+            "kind": None if src.get("kind") is None else np.ascontiguousarray(src["kind"], dtype=np.int32),
             "pointing": _f64(inp.get("pointing")),
             "gains": _cplx_as_f64(inp.get("gains")),
             "data": _cplx_as_f64(inp.get("data") if data is None else data),
@@ -97,7 +98,8 @@ class Problem:
             self.na, self.ntime, self.nchan, nsrc, tv,
             float(inp["ref_freq_hz"]), float(inp["beam_c"]), int(inp.get("beam_model", 0)),
             _ptr(k["uvw"]), _ptr(k["freq"]), _ptr(k["lm"]), _ptr(k["stokes"]),
-            _ptr(k["alpha"]), _ptr(k["shape"]), _ptr(k["pointing"]),
+            _ptr(k["alpha"]), _ptr(k["shape"]),
+            k["kind"].ctypes.data_as(_ip) if k["kind"] is not None else None, _ptr(k["pointing"]),
             _ptr(k["gains"]), _ptr(k["data"]), _ptr(k["weight"]))
 
     # ---- calls -----------------------------------------------------------

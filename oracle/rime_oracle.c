@@ -28,6 +28,11 @@
  * at the baseline (u_p - u_q, v_p - v_q) / lambda:
  *   g = exp(-pi^2 (major^2 u_maj^2 + minor^2 u_min^2) / (4 ln 2)),
  *   u_maj = u sin pa + v cos pa,  u_min = u cos pa - v sin pa.
+ * Sec. 1 names further morphologies (Sersic profiles among them) without a
+ * formula; kind 1 is the Sersic profile of index 1, an elliptical exponential
+ * disk exp(-r) in the coordinates (x_maj / major, x_min / minor) (major,
+ * minor the scale lengths, pa as above), whose unit-flux Fourier transform is
+ *   g = (1 + 4 pi^2 (major^2 u_maj^2 + minor^2 u_min^2))^(-3/2).
  * chi^2 uses Neumaier-compensated summation in the order (t, bl, k, c).
  *
  * Pinned by tests/test_oracle_pins.py (closed forms, invariants, an image-plane
@@ -197,6 +202,18 @@ static shape_term shape_factor(const rime_oracle_problem *P, int s, double du,
     double u = du / lambda, v = dv / lambda;
     double umaj = u * sin(pa) + v * cos(pa);
     double umin = u * cos(pa) - v * sin(pa);
+    if (P->kind && P->kind[s] == 1) {
+        /* exponential disk: g = (1 + q)^(-3/2), q = 4 pi^2 (major^2 u_maj^2 + minor^2 u_min^2),
+         * dg/dtheta = -3/2 (1 + q)^(-5/2) dq/dtheta */
+        double kd = 4.0 * PI * PI;
+        double q = kd * (maj * maj * umaj * umaj + mn * mn * umin * umin);
+        r.g = pow(1.0 + q, -1.5);
+        double dgdq = -1.5 * r.g / (1.0 + q);
+        r.dg_dmaj = dgdq * kd * 2.0 * maj * umaj * umaj;
+        r.dg_dmin = dgdq * kd * 2.0 * mn * umin * umin;
+        r.dg_dpa = dgdq * kd * (2.0 * maj * maj * umaj * umin - 2.0 * mn * mn * umin * umaj);
+        return r;
+    }
     double k = PI * PI / (4.0 * log(2.0));
     r.g = exp(-k * (maj * maj * umaj * umaj + mn * mn * umin * umin));
     r.dg_dmaj = r.g * (-k) * 2.0 * maj * umaj * umaj;

@@ -28,7 +28,10 @@ typedef struct {
     const double *lm;          /* [nsrc][2] radians */
     const double *stokes;      /* [nsrc][4] or [ntime][nsrc][4]: I, Q, U, V */
     const double *alpha;       /* [nsrc] spectral index */
-    const double *shape;       /* [nsrc][3] major FWHM, minor FWHM, pa; NULL = points */
+    const double *shape;       /* [nsrc][3] major, minor, pa; NULL = points */
+    const int *kind;           /* [nsrc] morphology of a source with a shape: 0 Gaussian
+                                  (major, minor = FWHM), 1 exponential disk (major, minor =
+                                  scale lengths); NULL = all Gaussian */
     const double *pointing;    /* [ntime][na][2] (dl, dm) or NULL */
     const double *gains;       /* [ntime][na][nchan][4] complex or NULL (identity) */
     const double *data;        /* [ntime][nbl][nchan][4] complex */

@@ -36,7 +36,7 @@ BAND_HZ = (1.0e9, 1.5e9)
 
 # Stream order is part of the recipe: never reorder, only append.
 _STREAMS = ("uvw", "lm", "stokes", "alpha", "shape", "gains", "noise",
-            "weights", "sets", "pointing")
+            "weights", "sets", "pointing", "kind")
 
 
 @dataclass(frozen=True)
@@ -133,7 +133,7 @@ def draw_sources(rs: dict, n: int, gauss_mask) -> dict:
 
 def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = None,
                 pointing_sigma: float = 0.0, time_varying: bool = False, noise: bool = True,
-                beam_model: int = 0, beam_c: float | None = None) -> dict:
+                beam_model: int = 0, beam_c: float | None = None, disk_fraction: float = 0.0) -> dict:
     """All inputs of one workload except the observed data (see ``observe``).
 
     precision "f32" rounds every real input to float32 values. noise=False
@@ -141,6 +141,9 @@ def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = N
     has its own stream), for timing runs that do not need the data values.
     beam_model: 0 the cos^3 beam of eq. 4, 1 the Jinc beam 2 J1(x)/x, with
     x = beam_c nu_GHz rho (beam_c defaults to BEAM_C).
+    disk_fraction: the share of the extended sources drawn as exponential
+    disks (sources["kind"] = 1; their shape axes are scale lengths) instead of
+    Gaussians; 0 leaves "kind" out.
     """
     if isinstance(wl, str):
         wl = WORKLOADS[wl]
@@ -151,6 +154,9 @@ def make_inputs(wl: Workload | str, precision: str = "f64", seed: int | None = N
     uvw = rs["uvw"].uniform(-1000.0, 1000.0, size=(nt, na, 3))
     freq = channel_freqs(nc)
     src = draw_sources(rs, wl.nsrc, np.arange(wl.nsrc) >= wl.npsrc)
+    if disk_fraction > 0.0:
+        disk = (np.arange(wl.nsrc) >= wl.npsrc) & (rs["kind"].uniform(size=wl.nsrc) < disk_fraction)
+        src["kind"] = disk.astype(np.int32)
     if time_varying:
         # brightness per (time, source): the static draw times U(0.5, 1.5)
         scale = rs["stokes"].uniform(0.5, 1.5, size=(nt, wl.nsrc, 1))
@@ -202,7 +208,7 @@ def round_f32(inp: dict) -> dict:
     out["ref_freq_hz"] = float(_r32(inp["ref_freq_hz"]))
     if inp.get("pointing") is not None:
         out["pointing"] = _r32(inp["pointing"])
-    out["sources"] = {k: _r32(v) for k, v in inp["sources"].items()}
+    out["sources"] = {k: (v if k == "kind" else _r32(v)) for k, v in inp["sources"].items()}
     if "sets" in inp:
         out["sets"] = dict(offsets=inp["sets"]["offsets"],
                            sources={k: _r32(v) for k, v in inp["sets"]["sources"].items()})

@@ -31,6 +31,9 @@ MUTANTS = [
     ("pointing sign", "hypot(l - dl, m - dm)", "hypot(l + dl, m - dm)"),
     ("gaussian axes swapped", "double umaj = u * sin(pa) + v * cos(pa);",
      "double umaj = u * cos(pa) + v * sin(pa);"),
+    ("disk exponent", "r.g = pow(1.0 + q, -1.5);", "r.g = pow(1.0 + q, -1.0);"),
+    ("disk constant", "double kd = 4.0 * PI * PI;", "double kd = 2.0 * PI * PI;"),
+    ("grad: disk derivative factor", "double dgdq = -1.5 * r.g / (1.0 + q);", "double dgdq = -1.5 * r.g;"),
     ("gaussian FWHM constant", "double k = PI * PI / (4.0 * log(2.0));",
      "double k = PI * PI / (2.0 * log(2.0));"),
     ("gaussian on u_p + u_q", "up[0] - uq[0], up[1] - uq[1], lambda);\n        cplx B[4];\n        brightness",

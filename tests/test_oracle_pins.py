@@ -189,6 +189,50 @@ def test_gaussian_shape_equals_image_plane_fourier_integral(pa):
     assert abs(g - ft) < 1e-10
 
 
+@pytest.mark.parametrize("pa", [0.0, 0.7, 2.5])
+def test_exponential_disk_equals_image_plane_fourier_integral(pa):
+    """kind 1 is the Sersic profile of index 1: an elliptical exponential disk
+    exp(-sqrt((x_maj/major)^2 + (x_min/minor)^2)) with scale lengths (major,
+    minor), major axis at pa from +m towards +l. Its shape factor is the
+    normalised 2-D Fourier transform, here by a trapezoid sum over +-30 scale
+    lengths (the cusp at the centre limits it to ~1e-6)."""
+    maj, mn, nu = 2e-5, 0.8e-5, 1.2e9
+    up, uq = np.array([1500.0, -800.0, 0.0]), np.array([0.0, 0.0, 0.0])
+    inp = problem(uvw=[[up, uq]], freq=[nu], lm=[[0.0, 0.0]], stokes=[1.0, 0, 0, 0],
+                  shape=[[maj, mn, pa]], ref_freq_hz=nu, beam_c=0.0)
+    inp["sources"]["kind"] = np.array([1], dtype=np.int32)
+    g = vis_all(inp)[0, 0, 0, 0]
+    lam = C_LIGHT / nu
+    u, v = (up[0] - uq[0]) / lam, (up[1] - uq[1]) / lam
+    L, n = 30 * maj, 3001
+    x = np.linspace(-L, L, n)
+    ll, mm = np.meshgrid(x, x, indexing="ij")
+    xmaj = ll * np.sin(pa) + mm * np.cos(pa)
+    xmin = ll * np.cos(pa) - mm * np.sin(pa)
+    img = np.exp(-np.sqrt(xmaj ** 2 / maj ** 2 + xmin ** 2 / mn ** 2))
+    ft = (img * np.exp(2j * np.pi * (u * ll + v * mm))).sum() / img.sum()
+    assert 0.05 < abs(ft) < 0.95
+    assert abs(g - ft) < 5e-6
+
+
+def test_exponential_disk_degenerate_cases_and_kind_zero():
+    """A disk with major = minor = 0 is a point; a circular disk does not depend
+    on pa; kind 0 (and no kind array) is the Gaussian."""
+    up = np.array([1200.0, 700.0, 0.0])
+    base = dict(uvw=[[up, np.zeros(3)]], freq=[1.3e9], lm=[[0.0, 0.0]],
+                stokes=[1.0, 0, 0, 0], ref_freq_hz=1.3e9, beam_c=0.0)
+
+    def g(shape, kind):
+        inp = problem(shape=[shape], **base)
+        if kind is not None:
+            inp["sources"]["kind"] = np.array([kind], dtype=np.int32)
+        return vis_all(inp)[0, 0, 0, 0]
+    assert g([0.0, 0.0, 1.0], 1) == 1.0
+    vals = [g([2e-5, 2e-5, pa], 1) for pa in (0.0, 0.4, 1.9)]
+    np.testing.assert_allclose(vals, vals[0], rtol=1e-14)
+    assert g([5e-5, 2e-5, 0.3], 0) == g([5e-5, 2e-5, 0.3], None) != g([5e-5, 2e-5, 0.3], 1)
+
+
 def test_gaussian_degenerate_cases():
     """maj = min = 0 is a point; maj = min gives a circular Gaussian whose
     value does not depend on pa."""
@@ -396,8 +440,11 @@ def _get_param(inp, s, j):
     return src["shape"][s, j - 7]
 
 
-def _fd_problem(beam_model=0):
+def _fd_problem(beam_model=0, disks=False):
     inp = _random_small(seed=5, na=4, ntime=2, nchan=3, npsrc=1, ngsrc=2, pointing=0.004)
+    if disks:
+        # the extended sources as exponential disks with scale lengths of the same size
+        inp["sources"]["kind"] = np.array([0, 1, 1], dtype=np.int32)
     # larger offsets so the beam derivative matters; data = model + noise
     inp["sources"]["lm"] *= 0.8
     if beam_model == 1:
@@ -408,9 +455,9 @@ def _fd_problem(beam_model=0):
     return inp
 
 
-@pytest.mark.parametrize("beam_model", [0, 1])
-def test_gradient_matches_central_differences_sources(beam_model):
-    inp = _fd_problem(beam_model)
+@pytest.mark.parametrize("beam_model,disks", [(0, False), (1, False), (0, True)])
+def test_gradient_matches_central_differences_sources(beam_model, disks):
+    inp = _fd_problem(beam_model, disks)
     chi, gs, _ = oracle.Problem(inp).chi2_grad(want_gains=False)
     assert chi == pytest.approx(oracle.Problem(inp).chi2(), rel=1e-13)
     nsrc = gs.shape[0]
