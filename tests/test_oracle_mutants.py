@@ -50,7 +50,10 @@ MUTANTS = [
     ("time-varying brightness index", "return P->stokes + 4 * ((long)t * P->nsrc + s);",
      "return P->stokes + 4 * ((long)s * P->ntime + t);"),
     ("grad: phase derivative sign", "r.dK_dl = r.K * IMAG *", "r.dK_dl = r.K * (-IMAG) *"),
-    ("grad: pa derivative sign", "- 2.0 * mn * mn * umin * umaj);", "+ 2.0 * mn * mn * umin * umaj);"),
+    ("grad: pa derivative sign", "r.g * (-k) * (2.0 * maj * maj * umaj * umin - 2.0 * mn * mn * umin * umaj);",
+     "r.g * (-k) * (2.0 * maj * maj * umaj * umin + 2.0 * mn * mn * umin * umaj);"),
+    ("grad: disk pa derivative sign", "dgdq * kd * (2.0 * maj * maj * umaj * umin - 2.0 * mn * mn * umin * umaj);",
+     "dgdq * kd * (2.0 * maj * maj * umaj * umin + 2.0 * mn * mn * umin * umaj);"),
     ("grad: beam derivative factor", "*dEx = -3.0 * c * c * sinc;", "*dEx = -3.0 * c * sinc;"),
     ("grad: gain q imaginary sign", "for (int c = 0; c < 4; c++) dVi[c] = -IMAG * dVr[c];",
      "for (int c = 0; c < 4; c++) dVi[c] = IMAG * dVr[c];"),
