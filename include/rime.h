@@ -81,16 +81,25 @@ typedef struct {
 } rime_dims;
 
 /* A sky model (Table 2: lm, brightness, gaussian shapes), structure of
- * arrays, double precision, host or device pointers. */
+ * arrays, double precision (kind: int32), host or device pointers. */
 typedef struct {
     int32_t nsrc;         /* >= 0 */
     int32_t time_varying; /* 0: stokes [nsrc][4]; 1: stokes [ntime][nsrc][4] (Table 2) */
     const double *lm;     /* [nsrc][2] direction cosines (l, m), l^2 + m^2 < 1 */
     const double *stokes; /* Stokes (I, Q, U, V) in Jy at nu_ref */
     const double *alpha;  /* [nsrc] spectral index (eq. 2) */
-    const double *shape;  /* [nsrc][3] (major FWHM, minor FWHM, pa) in rad,
-                             major >= minor >= 0; (0, 0, *) is a point source.
+    const double *shape;  /* [nsrc][3] (major, minor, pa) in rad, major >= minor >= 0,
+                             pa from +m towards +l; (0, 0, *) is a point source.
                              NULL: all sources are points. */
+    const int32_t *kind;  /* [nsrc] morphology of a source with a shape, or NULL (all 0):
+                             0 Gaussian, major / minor its FWHM:
+                               g = exp(-pi^2 (major^2 u_maj^2 + minor^2 u_min^2) / (4 ln 2));
+                             1 exponential disk (the Sersic profile of index 1 that
+                               Sec. 1 names), major / minor its scale lengths:
+                               g = (1 + 4 pi^2 (major^2 u_maj^2 + minor^2 u_min^2))^(-3/2);
+                             with (u_maj, u_min) = (u sin pa + v cos pa, u cos pa - v sin pa)
+                             the baseline (u_p - u_q, v_p - v_q) / lambda. Another value
+                             is RIME_E_INVALID (reported by the next waiting call). */
 } rime_sources;
 
 /* Number of baselines na*(na-1)/2 (Sec. 2.2). */

@@ -28,7 +28,7 @@ class rime_dims(C.Structure):
 
 class rime_sources(C.Structure):
     _fields_ = [("nsrc", C.c_int32), ("time_varying", C.c_int32), ("lm", C.c_void_p),
-                ("stokes", C.c_void_p), ("alpha", C.c_void_p), ("shape", C.c_void_p)]
+                ("stokes", C.c_void_p), ("alpha", C.c_void_p), ("shape", C.c_void_p), ("kind", C.c_void_p)]
 
 
 class rime_batch_config(C.Structure):
@@ -186,17 +186,20 @@ def rime_set_gains(ctx, gains):
     _check(lib().rime_set_gains(ctx, k.ptr(gains, np.complex128, "gains")), ctx)
 
 
-def make_sources(lm, stokes, alpha, shape=None, keep: _Keep | None = None) -> rime_sources:
+def make_sources(lm, stokes, alpha, shape=None, keep: _Keep | None = None, kind=None) -> rime_sources:
     k = keep if keep is not None else _Keep()
     nsrc = int(alpha.shape[0])
     tv = 1 if len(stokes.shape) == 3 else 0
     return rime_sources(nsrc, tv, k.ptr(lm, np.float64, "lm"), k.ptr(stokes, np.float64, "stokes"),
-                        k.ptr(alpha, np.float64, "alpha"), k.ptr(shape, np.float64, "shape"))
+                        k.ptr(alpha, np.float64, "alpha"), k.ptr(shape, np.float64, "shape"),
+                        k.ptr(kind, np.int32, "kind"))
 
 
-def rime_set_sources(ctx, lm, stokes, alpha, shape=None):
+def rime_set_sources(ctx, lm, stokes, alpha, shape=None, kind=None):
+    """kind: [nsrc] int32 morphology of the sources with a shape (0 Gaussian,
+    1 exponential disk) or None."""
     k = _Keep()
-    src = make_sources(lm, stokes, alpha, shape, k)
+    src = make_sources(lm, stokes, alpha, shape, k, kind)
     _check(lib().rime_set_sources(ctx, C.byref(src)), ctx)
 
 
@@ -246,13 +249,13 @@ def rime_destroy(ctx):
 
 
 def rime_chi2_noalloc(na, ntime, nchan, precision, freq_hz, uvw, pointing, data, weight, gains,
-                      lm, stokes, alpha, shape, chi2_dev, stream=0, ref_freq_hz=1.4e9, beam_c=65.0):
+                      lm, stokes, alpha, shape, chi2_dev, stream=0, ref_freq_hz=1.4e9, beam_c=65.0, kind=None):
     """The chi^2 entry point that allocates no device memory (see include/rime.h).
     Every array argument must be a device tensor; chi2_dev receives the value."""
     cd, rd = _ctype(precision)
     k = _Keep()
     dims = rime_dims(na, ntime, nchan, precision, ref_freq_hz, beam_c)
-    src = make_sources(lm, stokes, alpha, shape, k)
+    src = make_sources(lm, stokes, alpha, shape, k, kind)
     s = lib().rime_chi2_noalloc(C.byref(dims), k.ptr(freq_hz, np.float64, "freq_hz"),
                                 k.ptr(uvw, np.float64, "uvw"), k.ptr(pointing, np.float64, "pointing"),
                                 k.ptr(data, cd, "data"), k.ptr(weight, rd, "weight"),
@@ -261,14 +264,14 @@ def rime_chi2_noalloc(na, ntime, nchan, precision, freq_hz, uvw, pointing, data,
     _check(s, None)
 
 
-def rime_chi2_batched(ctx, src_offsets, lm, stokes, alpha, shape, chi2_dev):
+def rime_chi2_batched(ctx, src_offsets, lm, stokes, alpha, shape, chi2_dev, kind=None):
     """chi^2 of each source set against the context's observation.
     src_offsets: host int32 [nsets + 1]; the source arrays hold the
     concatenated sets; chi2_dev: float64 device tensor [nsets]."""
     off = np.ascontiguousarray(src_offsets, dtype=np.int32)
     nsets = int(off.shape[0]) - 1
     k = _Keep()
-    src = make_sources(lm, stokes, alpha, shape, k)
+    src = make_sources(lm, stokes, alpha, shape, k, kind)
     out = chi2_dev.data_ptr() if chi2_dev is not None and nsets > 0 else None
     _check(lib().rime_chi2_batched(ctx, nsets, off.ctypes.data, C.byref(src), out), ctx)
 

@@ -42,7 +42,7 @@ class Rime:
         A.rime_set_gains(self.ctx, gains)
 
     def set_sources(self, src: dict):
-        A.rime_set_sources(self.ctx, src["lm"], src["stokes"], src["alpha"], src.get("shape"))
+        A.rime_set_sources(self.ctx, src["lm"], src["stokes"], src["alpha"], src.get("shape"), src.get("kind"))
         self.nsrc = int(src["alpha"].shape[0])
 
     # calls ------------------------------------------------------------------
@@ -89,7 +89,7 @@ class Rime:
         if out is None:
             out = self.torch.empty(max(nsets, 0), dtype=self.torch.float64, device="cuda")
         A.rime_chi2_batched(self.ctx, offsets, sources["lm"], sources["stokes"], sources["alpha"],
-                            sources.get("shape"), out)
+                            sources.get("shape"), out, sources.get("kind"))
         self.nsrc = int(sources["alpha"].shape[0])
         return out
 

@@ -352,7 +352,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
         size_t ts = c->tsize();
         size_t ndc = (size_t)c->dims.ntime * cap * c->dims.na;
         Alloc alloc{c};
-        CK(c, alloc((void **)&c->d_src_in, (2 + 4 * rows + 1 + 3) * cap * sizeof(double)), "allocating sources");
+        CK(c, alloc((void **)&c->d_src_in, (2 + 4 * rows + 1 + 3 + 1) * cap * sizeof(double)), "allocating sources");
         CK(c, alloc(&c->d_stokes, rows * cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_gauss, cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_alpha, cap * ts), "allocating sources");
@@ -365,6 +365,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
     c->nsrc = src->nsrc;
     c->time_varying = src->time_varying;
     c->has_shape = src->shape != nullptr;
+    c->has_kind = src->shape != nullptr && src->kind != nullptr;
     if (n > 0) {
         CK(c, cudaMemcpyAsync(c->src_lm(), src->lm, n * 2 * sizeof(double), cudaMemcpyDefault, c->stream),
            "copying lm");
@@ -375,6 +376,9 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
         if (src->shape)
             CK(c, cudaMemcpyAsync(c->src_shape(), src->shape, n * 3 * sizeof(double), cudaMemcpyDefault,
                                   c->stream), "copying shape");
+        if (c->has_kind)
+            CK(c, cudaMemcpyAsync(c->src_kind(), src->kind, n * sizeof(int32_t), cudaMemcpyDefault, c->stream),
+               "copying kind");
     }
     CK(c, reset_class(c, EC_SRC), "reset status");
     CK(c, reset_class(c, EC_MODE), "reset status");

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
                 for (int i = 0; i < TP; i++) ap[i] = Ar[s * ASTRIDE + pl + i];
 #pragma unroll
                 for (int j = 0; j < TQ; j++) aq[j] = Ac[s * ASTRIDE + ql + j];
-                const bool is_gauss = gq.w != 0.0;
+                const bool is_gauss = gq.w != 0.0, is_disk = gq.w > 1.5;
 #pragma unroll
                 for (int i = 0; i < TP; i++)
 #pragma unroll
@@ -213,7 +213,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
                         double zr = ap[i].x * aq[j].x + ap[i].y * aq[j].y;
                         double zi = ap[i].y * aq[j].x - ap[i].x * aq[j].y;
                         if (is_gauss) {
-                            double g = exp(gq.x * du2[b] + gq.y * dudv[b] + gq.z * dv2[b]);
+                            // Gaussian exp(e); exponential disk (1 + e)^(-3/2)
+                            const double e = gq.x * du2[b] + gq.y * dudv[b] + gq.z * dv2[b];
+                            double g;
+                            if (is_disk) {
+                                const double r = rsqrt(1.0 + e);
+                                g = r * r * r;
+                            } else {
+                                g = exp(e);
+                            }
                             zr *= g;
                             zi *= g;
                         }
@@ -404,18 +412,27 @@ __device__ __forceinline__ void accumulate2g(Pair &acc, float2 ax, float2 ay, fl
         acc.im[c] = __ffma2_rn(zi, X[c], acc.im[c]);
     }
 }
-// Gaussian factors of two slots: 2^(Qf(x_p) + Qf(x_q) - x_p . L(x_q)), log2 units
-__device__ __forceinline__ float2 gauss2(float2 qp, float2 up, float2 vp, float2 qq, float2 lx, float2 ly) {
+// Shape factors of two slots from the quadratic form e = Qf(x_p) + Qf(x_q) -
+// x_p . L(x_q) of the baseline: Gaussian 2^e (log2 units), exponential disk
+// (1 + e)^(-3/2) (only in the kernels built for general sky models).
+template <bool GENERAL>
+__device__ __forceinline__ float2 shape2(bool disk, float2 qp, float2 up, float2 vp, float2 qq, float2 lx, float2 ly) {
     const float2 e = __ffma2_rn(f2(-up.x, -up.y), lx, __ffma2_rn(f2(-vp.x, -vp.y), ly, __fadd2_rn(qp, qq)));
+    if (GENERAL && disk) {
+        const float r0 = rsqrtf(1.0f + e.x), r1 = rsqrtf(1.0f + e.y);
+        return f2(r0 * r0 * r0, r1 * r1 * r1);
+    }
     return f2(ex2_approx(e.x), ex2_approx(e.y));
 }
 
 // One work item: timestep t, channel k, antenna unit u, sources [sb, se).
-// Returns the block's chi^2 (in thread 0; chi^2 modes only). JINC selects the
-// beam model at compile time: this kernel runs at its register limit, and a
+// Returns the block's chi^2 (in thread 0; chi^2 modes only). GENERAL = false
+// builds the kernel for eq. 4's cos^3 beam and point / Gaussian sources
+// alone; GENERAL = true takes the beam model from the channel constants and
+// the exponential disks too. The kernel runs at its register limit: a
 // run-time choice (the Bessel function's code beside cos^3 in the staging
-// loop) cost it 1.5 %.
-template <int MODE, bool JINC>
+// loop) cost the common case 1.5 %.
+template <int MODE, bool GENERAL>
 __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se) {
     constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     const int tid = threadIdx.x;
@@ -504,7 +521,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         for (int s = it_s0, a = it_a0; s < sc;) {
             float2 v = phase_factor(S.rTau[s * NLOC + a], ch);
             if (pointing) {
-                float E = beam_E(JINC ? RIME_BEAM_JINC : RIME_BEAM_COS3, ch.cnu * S.rRho[s * NLOC + a]);
+                float E = beam_E(GENERAL ? ch.beam : RIME_BEAM_COS3, ch.cnu * S.rRho[s * NLOC + a]);
                 v.x *= E;
                 v.y *= E;
             }
@@ -529,7 +546,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             // spectral factor (nu / nu_ref)^alpha = 2^(2 alpha hlr) of eq. 2
             float f = exp2f(2.0f * S.rAl[tid] * ch.hlr);
             if (!pointing) {
-                float E = beam_E(JINC ? RIME_BEAM_JINC : RIME_BEAM_COS3, ch.cnu * S.rRho[tid * NLOC]);
+                float E = beam_E(GENERAL ? ch.beam : RIME_BEAM_COS3, ch.cnu * S.rRho[tid * NLOC]);
                 f *= E * E;
             }
             float4 st = S.rSt[tid];
@@ -556,6 +573,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 const float2 bx[4] = {f2(bx01.x, bx01.y), f2(bx01.z, bx01.w), f2(bx23.x, bx23.y), f2(bx23.z, bx23.w)};
                 const float2 by[4] = {f2(by01.x, by01.y), f2(by01.z, by01.w), f2(by23.x, by23.y), f2(by23.z, by23.w)};
                 if (S.Gf[s] != 0.f) {
+                    const bool disk = S.Gf[s] > 1.5f;
                     const float qps = S.Qr[s * RSTR + ip];
                     const float2 qp = f2(qps, qps);
                     const float4 *qv = reinterpret_cast<const float4 *>(QC + s * cstr + iq);
@@ -564,8 +582,10 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const float4 q4 = qv[h], lx4 = lxv[h], ly4 = lyv[h];
-                        const float2 g0 = gauss2(qp, up, vp, f2(q4.x, q4.y), f2(lx4.x, lx4.y), f2(ly4.x, ly4.y));
-                        const float2 g1 = gauss2(qp, up, vp, f2(q4.z, q4.w), f2(lx4.z, lx4.w), f2(ly4.z, ly4.w));
+                        const float2 g0 = shape2<GENERAL>(disk, qp, up, vp, f2(q4.x, q4.y), f2(lx4.x, lx4.y),
+                                                          f2(ly4.x, ly4.y));
+                        const float2 g1 = shape2<GENERAL>(disk, qp, up, vp, f2(q4.z, q4.w), f2(lx4.z, lx4.w),
+                                                          f2(ly4.z, ly4.w));
                         accumulate2g(acc[2 * h], ax, ay, bx[2 * h], by[2 * h], g0, s01, s23);
                         accumulate2g(acc[2 * h + 1], ax, ay, bx[2 * h + 1], by[2 * h + 1], g1, s01, s23);
                     }
@@ -589,7 +609,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 const float *kx = S.Kx + s * RSTR, *ky = S.Ky + s * RSTR;
                 const float2 ax[2] = {f2(kx[ho[0]], kx[ho[0]]), f2(kx[ho[4]], kx[ho[4]])};
                 const float2 ay[2] = {f2(ky[ho[0]], ky[ho[0]]), f2(ky[ho[4]], ky[ho[4]])};
-                const bool is_gauss = S.Gf[s] != 0.f;
+                const bool is_gauss = S.Gf[s] != 0.f, disk = S.Gf[s] > 1.5f;
                 const float *qq = S.Qr + s * RSTR, *lx = S.Lxr + s * RSTR, *ly = S.Lyr + s * RSTR;
 #pragma unroll
                 for (int h = 0; h < 4; h++) {
@@ -598,7 +618,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                     const float2 bx = f2(kx[c0], kx[c1]), by = f2(ky[c0], ky[c1]);
                     if (is_gauss) {
                         const float qps = qq[ho[4 * r2]];
-                        const float2 g = gauss2(f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]),
+                        const float2 g = shape2<GENERAL>(disk, f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]),
                                                 f2(lx[c0], lx[c1]), f2(ly[c0], ly[c1]));
                         accumulate2g(acc[h], ax[r2], ay[r2], bx, by, g, s01, s23);
                     } else {
@@ -721,7 +741,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     return bsum;
 }
 
-template <int MODE, bool JINC>
+template <int MODE, bool GENERAL>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -731,7 +751,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
     const int t = P.t_begin + rest / P.nchan;
-    const double bsum = fused_item<MODE, JINC>(P, S, t, k, u, 0, P.nsrc);
+    const double bsum = fused_item<MODE, GENERAL>(P, S, t, k, u, 0, P.nsrc);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
 }
 
@@ -742,7 +762,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
 // item share their data, weights and gains, which the later sets read from
 // L1. One partial per (set, t, channel, unit): the sums do not depend on the
 // schedule.
-template <bool JINC>
+template <bool GENERAL>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(const FusedParams P, const BatchParams B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
@@ -765,7 +785,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(co
         for (int rank = g * B.gsets; rank < r1; rank++) {
             const int j = B.order[rank];
             for (int k = kc * B.cpi; k < k1; k++) {
-                const double bsum = fused_item<MODE_CHI2, JINC>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
+                const double bsum = fused_item<MODE_CHI2, GENERAL>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
                 if (threadIdx.x == 0)
                     B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
                 __syncthreads();
@@ -950,7 +970,7 @@ cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, lon
         }
     }
     size_t sm = sizeof(f32::Smem);
-    if (c->beam_model == RIME_BEAM_JINC) switch (mode) {
+    if (c->beam_model != RIME_BEAM_COS3 || c->has_kind) switch (mode) {
             case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, true>, P, blocks, f32::THREADS, sm, c->stream);
             case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, true>, P, blocks, f32::THREADS, sm, c->stream);
             default: return launch_k(f32::k_fused_f32<MODE_GRAD, true>, P, blocks, f32::THREADS, sm, c->stream);
@@ -967,7 +987,8 @@ cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid) {
     fill_fused_params(c, P, nullptr, nullptr, nullptr, nullptr);
     if (grid <= 0 || B.nitems == 0) return cudaSuccess;
     const size_t sm = sizeof(f32::Smem);
-    auto kern = c->beam_model == RIME_BEAM_JINC ? f32::k_batched_f32<true> : f32::k_batched_f32<false>;
+    auto kern = (c->beam_model != RIME_BEAM_COS3 || c->has_kind) ? f32::k_batched_f32<true>
+                                                                  : f32::k_batched_f32<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     kern<<<grid, f32::THREADS, sm, c->stream>>>(P, B);

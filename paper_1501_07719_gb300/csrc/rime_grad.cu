@@ -54,6 +54,7 @@ struct GradParams {
     int chan_group, ncg;          // channels per block, channel groups
     long long nbl;
     int has_pointing;
+    int has_disk;                // the sky model may hold exponential disks (a kind array was given)
     double ref_freq_hz;
     const Unit *units;
     const uint16_t *bls;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     const T *st = reinterpret_cast<const T *>(P.stokes) + 4 * sidx;
     const T sI = st[0], sQ = st[1], sU = st[2], sV = st[3];
     const T *gq = reinterpret_cast<const T *>(P.gauss) + 4 * sidx;
-    const bool is_gauss = gq[3] != T(0);
+    const bool is_gauss = gq[3] != T(0), is_disk = gq[3] > T(1.5);
     const T *extra = reinterpret_cast<const T *>(P.extra) + 8 * sidx;
     const double l = extra[0], m = extra[1], l_n = extra[2], m_n = extra[3];
     const double maj = extra[4], mn = extra[5], sp = extra[6], cp = extra[7];
@@ -276,8 +277,17 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
                 const T2 ap = sA[oa + sl], aq = sA[ob + sl];
                 T zr = ap.x * aq.x + ap.y * aq.y;   // z = A_p conj(A_q)
                 T zi = ap.y * aq.x - ap.x * aq.y;
+                T hq = T(1);   // (dg/dq) / g in units of the form's derivative: 1 Gaussian, -3/2 / (1 + q) disk
                 if (is_gauss) {
-                    const T g = gexp(gA * du * du + gB * du * dv + gC * dv * dv);
+                    const T e = gA * du * du + gB * du * dv + gC * dv * dv;
+                    T g;
+                    if (is_disk) {
+                        const T r = rsqrt(T(1) + e);
+                        g = r * r * r;
+                        hq = T(-1.5) * r * r;
+                    } else {
+                        g = gexp(e);
+                    }
                     zr *= g;
                     zi *= g;
                 }
@@ -293,9 +303,10 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
                 acc[5] += im * dv;
                 acc[6] += im * dw;
                 if (is_gauss) {
-                    acc[7] += re * du * du;
-                    acc[8] += re * du * dv;
-                    acc[9] += re * dv * dv;
+                    const T rh = re * hq;
+                    acc[7] += rh * du * du;
+                    acc[8] += rh * du * dv;
+                    acc[9] += rh * dv * dv;
                 }
                 if (pointing) {
                     const T2 ep = sE[oa + sl], eq = sE[ob + sl];
@@ -328,9 +339,11 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
         out[5] += (double)(w * acc[3]);
         out[6] += (double)(w * aR * lnr);
         if (is_gauss) {
-            // ln g = nu^2 (A du^2 + B du dv + C dv^2), A = -K (maj^2 sp^2 + min^2 cp^2),
-            // B = -2 K sp cp (maj^2 - min^2), C = -K (maj^2 cp^2 + min^2 sp^2), K = pi^2/(4 ln 2 c^2)
-            const T K = T(kGaussK / (kCLight * kCLight)) * nu * nu;
+            // Gaussian: ln g = nu^2 (A du^2 + B du dv + C dv^2), A = -K (maj^2 sp^2 + min^2 cp^2),
+            // B = -2 K sp cp (maj^2 - min^2), C = -K (maj^2 cp^2 + min^2 sp^2), K = pi^2/(4 ln 2 c^2);
+            // disk: q = the same form with -K -> 4 pi^2 / c^2, its -3/2 / (1 + q) in the moments
+            const T K = is_disk ? T(-4.0 * kPi * kPi / (kCLight * kCLight)) * nu * nu
+                                : T(kGaussK / (kCLight * kCLight)) * nu * nu;
             const T mj = (T)maj, mi = (T)mn, sps = (T)sp, cps = (T)cp;
             const T dd = mj * mj - mi * mi;
             const T Au = acc[7], Auv = acc[8], Av = acc[9];
@@ -419,15 +432,17 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     // ---- per-source constants of this thread's two sources (the rest is read
     // from the L1-resident tables once per channel, outside the baseline loop)
     int sidx[2];
-    bool sact[2], is_gauss[2];
+    bool sact[2], is_gauss[2], is_disk[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
         const int s = sch * SG + 2 * sp + h;
         sact[h] = s < P.nsrc;
         sidx[h] = sact[h] ? s : P.nsrc - 1;
         is_gauss[h] = reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] != T(0);
+        is_disk[h] = P.has_disk && reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] > T(1.5);
     }
     const bool any_gauss = is_gauss[0] || is_gauss[1];
+    const bool any_disk = is_disk[0] || is_disk[1];
     const float4 st0 = reinterpret_cast<const float4 *>(P.stokes)[sidx[0]];
     const float4 st1 = reinterpret_cast<const float4 *>(P.stokes)[sidx[1]];
     const float2 sI = pf2(st0.x, st1.x), sQ = pf2(st0.y, st1.y);
@@ -507,9 +522,19 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 // z = A_p conj(A_q) for both sources
                 float2 zr = __ffma2_rn(apr, aqr, __fmul2_rn(api, aqi));
                 float2 zi = __ffma2_rn(api, aqr, __fmul2_rn(pf2(-apr.x, -apr.y), aqi));
+                float2 hq = pf2(1.f, 1.f);   // as in k_grad_src: 1 Gaussian, -3/2 / (1 + q) disk
                 if (any_gauss) {
                     const float2 e = __ffma2_rn(gA, pdup(du * du), __ffma2_rn(gB, pdup(du * dv), __fmul2_rn(gC, pdup(dv * dv))));
-                    const float2 g = pf2(exp2f(e.x), exp2f(e.y));
+                    float2 g;
+                    if (any_disk) {
+                        const float r0 = rsqrtf(1.f + e.x), r1 = rsqrtf(1.f + e.y);
+                        g.x = is_disk[0] ? r0 * r0 * r0 : exp2f(e.x);
+                        g.y = is_disk[1] ? r1 * r1 * r1 : exp2f(e.y);
+                        hq.x = is_disk[0] ? -1.5f * r0 * r0 : 1.f;
+                        hq.y = is_disk[1] ? -1.5f * r1 * r1 : 1.f;
+                    } else {
+                        g = pf2(exp2f(e.x), exp2f(e.y));
+                    }
                     zr = __fmul2_rn(zr, g);
                     zi = __fmul2_rn(zi, g);
                 }
@@ -530,9 +555,10 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 acc[5] = __ffma2_rn(im, pdup(dv), acc[5]);
                 acc[6] = __ffma2_rn(im, pdup(dw), acc[6]);
                 if (any_gauss) {
-                    acc[7] = __ffma2_rn(re, pdup(du * du), acc[7]);
-                    acc[8] = __ffma2_rn(re, pdup(du * dv), acc[8]);
-                    acc[9] = __ffma2_rn(re, pdup(dv * dv), acc[9]);
+                    const float2 rh = any_disk ? __fmul2_rn(re, hq) : re;
+                    acc[7] = __ffma2_rn(rh, pdup(du * du), acc[7]);
+                    acc[8] = __ffma2_rn(rh, pdup(du * dv), acc[8]);
+                    acc[9] = __ffma2_rn(rh, pdup(dv * dv), acc[9]);
                 }
                 if (pointing) {
                     const float4 ep = *reinterpret_cast<const float4 *>(sE + oa + 2 * sp);
@@ -572,7 +598,8 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
             out[h][5] += (double)(w * a[3]);
             out[h][6] += (double)(w * aR * lnr);
             if (is_gauss[h]) {
-                const T K = T(kGaussK / (kCLight * kCLight)) * nu * nu;
+                const T K = is_disk[h] ? T(-4.0 * kPi * kPi / (kCLight * kCLight)) * nu * nu
+                                       : T(kGaussK / (kCLight * kCLight)) * nu * nu;
                 const T mj = ex[4], mi = ex[5], sps = ex[6], cps = ex[7];
                 const T dd = mj * mj - mi * mi;
                 const T Au = a[7], Auv = a[8], Av = a[9];
@@ -690,6 +717,7 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     P.ncg = ncg;
     P.nbl = c->nbl;
     P.has_pointing = c->has_pointing;
+    P.has_disk = c->has_kind;
     P.ref_freq_hz = c->dims.ref_freq_hz;
     P.units = c->d_gunits;
     P.bls = c->d_gbl;

@@ -176,11 +176,13 @@ struct rime_ctx {
     bool sources_set = false;
     size_t src_cap = 0;               // sources the buffers below can hold
     size_t src_stokes_rows = 0;       // 1 or ntime
-    double *d_src_in = nullptr;       // copy of the FP64 parameters: lm, stokes, alpha, shape
+    double *d_src_in = nullptr;       // copy of the FP64 parameters: lm, stokes, alpha, shape, kind
     double *src_lm() const { return d_src_in; }
     double *src_stokes() const { return d_src_in + 2 * src_cap; }
     double *src_alpha() const { return d_src_in + 2 * src_cap + 4 * src_cap * src_stokes_rows; }
     double *src_shape() const { return src_alpha() + src_cap; }
+    int32_t *src_kind() const { return reinterpret_cast<int32_t *>(src_shape() + 3 * src_cap); }
+    bool has_kind = false;            // a kind array was given (disks may be present)
     bool has_shape = false;
     void *d_stokes = nullptr, *d_gauss = nullptr, *d_alpha = nullptr;
     void *d_src_extra = nullptr;      // per source: l, m, l/n, m/n, major, minor, sin pa, cos pa

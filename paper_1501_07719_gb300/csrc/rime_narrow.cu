@@ -98,10 +98,19 @@ __device__ __forceinline__ double beam_of(double rho, const ChanD &ch) { return 
 // (nu / nu_ref)^alpha = 2^(2 alpha hlr)
 __device__ __forceinline__ float spectral(float alpha, const ChanF &ch) { return exp2f(2.0f * alpha * ch.hlr); }
 __device__ __forceinline__ double spectral(double alpha, const ChanD &ch) { return exp2(2.0 * alpha * ch.hlr); }
-// Gaussian factor from the exponent (log2 units in FP32, natural in FP64,
-// as the upload kernel stores the coefficients)
+// Shape factor from the quadratic form e of the baseline: Gaussian exp(e)
+// (log2 units in FP32, natural in FP64, as the upload kernel stores the
+// coefficients), exponential disk (1 + e)^(-3/2)
 __device__ __forceinline__ float gauss_of(float e) { return ex2_approx(e); }
 __device__ __forceinline__ double gauss_of(double e) { return exp(e); }
+__device__ __forceinline__ float disk_of(float e) {
+    const float r = rsqrtf(1.0f + e);
+    return r * r * r;
+}
+__device__ __forceinline__ double disk_of(double e) {
+    const double r = rsqrt(1.0 + e);
+    return r * r * r;
+}
 __device__ __forceinline__ float nu2_of(const ChanF &ch) { return ch.nu2; }
 __device__ __forceinline__ double nu2_of(const ChanD &ch) { return ch.nu2; }
 
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
 #pragma unroll 2
         for (int s = 0; s < sc; s++) {
             const T4 g = sG[s];
-            const bool is_gauss = g.w != T(0);
+            const bool is_gauss = g.w != T(0), is_disk = g.w > T(1.5);
 #pragma unroll
             for (int i = 0; i < M; i++) {
                 if (!act[i]) continue;
@@ -233,7 +242,7 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
                 T zi = ap.y * aq.x - ap.x * aq.y;
                 if (is_gauss) {
                     const T e = g.x * du2[i] + g.y * dudv[i] + g.z * dv2[i];
-                    const T gg = gauss_of(e);
+                    const T gg = is_disk ? disk_of(e) : gauss_of(e);
                     zr *= gg;
                     zi *= gg;
                 }

@@ -131,7 +131,7 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     size_t o_chan = L.take((size_t)dims->nchan * sizeof(ChanF) * 2);
     size_t o_uvwf = L.take(dims->precision == RIME_FP32 ? nta * sizeof(float4) : 0);
     size_t o_gains = L.take(gains ? nta * dims->nchan * 8 * ts : 0);
-    size_t o_srcin = L.take((2 + 4 * rows + 1 + 3) * cap * sizeof(double));
+    size_t o_srcin = L.take((2 + 4 * rows + 1 + 3 + 1) * cap * sizeof(double));
     size_t o_stokes = L.take(rows * cap * 4 * ts);
     size_t o_gauss = L.take(cap * 4 * ts);
     size_t o_alpha = L.take(cap * ts);
@@ -184,6 +184,7 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     c.nsrc = (int)nsrc;
     c.time_varying = src->time_varying;
     c.has_shape = src->shape != nullptr;
+    c.has_kind = src->shape != nullptr && src->kind != nullptr;
     c.sources_set = true;
 
 #define CKN(call)                                                     \
@@ -203,6 +204,8 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
         if (src->shape)
             CKN(cudaMemcpyAsync(c.src_shape(), src->shape, nsrc * 3 * sizeof(double), cudaMemcpyDefault,
                                 c.stream));
+        if (c.has_kind)
+            CKN(cudaMemcpyAsync(c.src_kind(), src->kind, nsrc * sizeof(int32_t), cudaMemcpyDefault, c.stream));
     }
     CKN(launch_prep_channels(&c));
     CKN(launch_validate_uvw(&c));

@@ -95,8 +95,8 @@ __global__ void k_convert_gains(long long n, const double *in, T *out, DevStatus
 // The FP32 path stores A, B, C scaled by log2(e) for an exp2.
 template <typename T>
 __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, const double *stokes,
-                               const double *alpha, const double *shape, T *o_stokes, T *o_gauss,
-                               T *o_alpha, T *o_extra, DevStatus *st) {
+                               const double *alpha, const double *shape, const int32_t *kind, T *o_stokes,
+                               T *o_gauss, T *o_alpha, T *o_extra, DevStatus *st) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nst = (long long)stokes_rows * nsrc;
     if (i < nst) {
@@ -121,18 +121,29 @@ __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, cons
         flag(st, EC_SRC, EB_NONFINITE, i);
     else if (!(l * l + m * m < 1.0) || !(mn >= 0.0) || !(maj >= mn))
         flag(st, EC_SRC, EB_RANGE, i);
+    const int kd = kind ? kind[i] : 0;
+    if (kd != 0 && kd != 1) flag(st, EC_SRC, EB_RANGE, i);
     double sp, cp;
     sincos(pa, &sp, &cp);
-    double k = -kGaussK / (kCLight * kCLight);
-    if (sizeof(T) == 4) k *= kLog2e;
+    // the shape factor's quadratic form in the baseline (du, dv) in metres,
+    // times nu^2 in the kernels: Gaussian exponent -pi^2/(4 ln 2) (... )/c^2
+    // (log2 units in FP32, for ex2), disk q = 4 pi^2 (...)/c^2 in g = (1+q)^-3/2
+    double k;
+    if (kd == 1) {
+        k = 4.0 * kPi * kPi / (kCLight * kCLight);
+    } else {
+        k = -kGaussK / (kCLight * kCLight);
+        if (sizeof(T) == 4) k *= kLog2e;
+    }
     double A = k * (maj * maj * sp * sp + mn * mn * cp * cp);
     double B = k * 2.0 * sp * cp * (maj * maj - mn * mn);
     double C = k * (maj * maj * cp * cp + mn * mn * sp * sp);
-    bool gauss = (maj != 0.0 || mn != 0.0);
+    bool extended = (maj != 0.0 || mn != 0.0);
     o_gauss[4 * i + 0] = (T)A;
     o_gauss[4 * i + 1] = (T)B;
     o_gauss[4 * i + 2] = (T)C;
-    o_gauss[4 * i + 3] = gauss ? T(1) : T(0);
+    // 0 point, 1 Gaussian, 2 exponential disk
+    o_gauss[4 * i + 3] = extended ? T(kd == 1 ? 2 : 1) : T(0);
     o_alpha[i] = (T)a;
     if (o_extra) {
         // for the gradient: l, m, l/n, m/n, major, minor, sin pa, cos pa
@@ -252,13 +263,14 @@ cudaError_t launch_prep_sources(rime_ctx *c) {
     int rows = c->time_varying ? c->dims.ntime : 1;
     long long n = (long long)rows * nsrc;
     const double *shape = c->has_shape ? c->src_shape() : nullptr;
+    const int32_t *kind = c->has_kind ? c->src_kind() : nullptr;
     if (c->dims.precision == RIME_FP64)
         k_prep_sources<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
-            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (double *)c->d_stokes,
+            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, kind, (double *)c->d_stokes,
             (double *)c->d_gauss, (double *)c->d_alpha, (double *)c->d_src_extra, c->d_status);
     else
         k_prep_sources<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
-            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, (float *)c->d_stokes,
+            nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, kind, (float *)c->d_stokes,
             (float *)c->d_gauss, (float *)c->d_alpha, (float *)c->d_src_extra, c->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -17,10 +17,10 @@ JINC = dict(beam_model=1, beam_c=262.0)
 
 
 def make_case(wl, precision="f64", pointing_sigma=0.0, time_varying=False, seed=None,
-              gains=True, unit_weights=None, beam_model=0, beam_c=None):
+              gains=True, unit_weights=None, beam_model=0, beam_c=None, disk_fraction=0.0):
     inp = rime_synth.make_inputs(wl, precision=precision, seed=seed,
                                  pointing_sigma=pointing_sigma, time_varying=time_varying,
-                                 beam_model=beam_model, beam_c=beam_c)
+                                 beam_model=beam_model, beam_c=beam_c, disk_fraction=disk_fraction)
     if not gains:
         inp["gains"] = None
     if unit_weights:

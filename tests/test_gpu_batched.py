@@ -102,6 +102,28 @@ def test_batched_equals_plain_per_set(precision, kernel):
     r.close()
 
 
+@pytest.mark.parametrize("kernel", [None, "tiled"])
+def test_batched_with_exponential_disks(kernel):
+    """Sets whose extended sources are partly exponential disks (source kind 1):
+    each set against the oracle, and equal to its plain call."""
+    inp = _case("13ant", "f32")
+    sets = inp["sets"]
+    rng = np.random.default_rng(5)
+    ext = sets["sources"]["shape"][:, 0] > 0
+    sets["sources"]["kind"] = (ext & (rng.uniform(size=ext.size) < 0.5)).astype(np.int32)
+    assert sets["sources"]["kind"].sum() > 0
+    r = gpu_ctx(inp, "f32")
+    _kernel(r, kernel)
+    got = _run(r, sets)
+    for j in range(nsets(sets)):
+        want = oracle.Problem(inp, sources=set_sources(sets, j), data=inp["data"]).chi2()
+        assert rel_err(got[j], want) <= TOL["f32"]["chi2"], (j, got[j], want)
+        r.set_sources(set_sources(sets, j))
+        plain = r.chi2()
+        assert abs(got[j] - plain) <= 1e-12 * plain, j
+    r.close()
+
+
 def test_batched_configurations_agree_bitwise():
     inp = _case("13ant", "f32")
     sets = inp["sets"]

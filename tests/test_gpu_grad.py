@@ -34,6 +34,10 @@ CASES = {
     # the Jinc beam's derivative, per antenna and folded
     "10ant-jinc-pointing": dict(wl=rime_synth.custom(10, 2, 4, 5, 5, seed_index=58), pointing_sigma=0.004, **JINC),
     "12ant-jinc": dict(wl=rime_synth.custom(12, 2, 3, 6, 4, seed_index=59), **JINC),
+    # exponential disks beside Gaussians: the shape derivatives of both
+    "11ant-disks": dict(wl=rime_synth.custom(11, 2, 3, 4, 12, seed_index=60), disk_fraction=0.5),
+    "10ant-disks-pointing": dict(wl=rime_synth.custom(10, 2, 3, 3, 9, seed_index=61), disk_fraction=0.6,
+                                 pointing_sigma=0.003),
 }
 
 

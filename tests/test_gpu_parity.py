@@ -46,6 +46,12 @@ CASES = {
                                 **JINC),
     "70ant-jinc": dict(wl=rime_synth.custom(70, 2, 3, 6, 5, seed_index=37), **JINC),
     "20ant-jinc": dict(wl=rime_synth.custom(20, 2, 3, 9, 9, seed_index=38), **JINC),
+    # exponential disks (source kind 1) beside Gaussians and points; with the
+    # Jinc beam and pointing errors too, across antenna units
+    "13ant-disks": dict(wl=rime_synth.custom(13, 3, 5, 10, 27, seed_index=39), disk_fraction=0.5,
+                        time_varying=True),
+    "70ant-disks-jinc": dict(wl=rime_synth.custom(70, 2, 3, 6, 11, seed_index=40), disk_fraction=0.5,
+                             pointing_sigma=0.002, **JINC),
 }
 
 

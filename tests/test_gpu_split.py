@@ -102,6 +102,20 @@ def test_split_without_sources_gives_zero_model():
     assert rel_err(chi, want) <= 1e-6
 
 
+def test_split_rejects_exponential_disks():
+    import paper_1501_07719_gb300 as R
+    inp = make_case(rime_synth.custom(8, 2, 2, 3, 4, seed_index=82), "f32", disk_fraction=1.0)
+    assert inp["sources"]["kind"].sum() == 4
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(R.RIME_TC_SPLIT_TF32)
+    with pytest.raises(R.RimeError) as e:
+        r.chi2()
+    assert e.value.status == R._abi.RIME_E_INVALID and "point sources" in str(e.value)
+    r.set_tensor_mode(R.RIME_TC_OFF)
+    assert rel_err(r.chi2(), oracle.Problem(inp, data=inp["data"]).chi2()) <= 1e-4
+    r.close()
+
+
 def test_split_rejects_gaussian_sources_and_fp64():
     import paper_1501_07719_gb300 as R
     inp = make_case(rime_synth.custom(8, 2, 2, 3, 2, seed_index=78), "f32")
