@@ -463,7 +463,11 @@ rime_status rime_chi2_grad(rime_ctx *c, double *chi2, double *grad_src, void *gr
     if (gg)
         CK(c, cudaMemsetAsync(gg, 0, (size_t)c->dims.ntime * c->dims.na * c->dims.nchan * 8 * sizeof(double),
                               c->stream), "clearing grad_gains");
-    CK(c, launch_fused_mode(c, MODE_GRAD, nullptr, &c->d_status->chi2, c->d_yadj, gg), "gradient forward kernel");
+    if (narrow_applies(c))
+        CK(c, launch_narrow(c, MODE_GRAD, nullptr, &c->d_status->chi2, 0, c->nsrc, c->d_yadj, gg),
+           "gradient forward kernel");
+    else
+        CK(c, launch_fused_mode(c, MODE_GRAD, nullptr, &c->d_status->chi2, c->d_yadj, gg), "gradient forward kernel");
     CK(c, launch_grad_src(c, grad_src), "source gradient kernels");
     rime_status s = sync_status(c);
     if (s != RIME_OK) return s;

@@ -57,6 +57,41 @@ __device__ void finish_chi2(double block_value, const FusedParams &P, double *re
     }
 }
 
+// Adjoint of the chi^2 term of one visibility (eq. 7 through eq. 1):
+//   Sh = 2 w G_p^H R G_q with R = V - D; for a source with coherency c B0
+//   (eq. 2), d chi^2 = Re(c sum_X X Y_X) with
+//   Y_I = conj(Sh00 + Sh11), Y_Q = conj(Sh00 - Sh11), Y_U = conj(Sh01 + Sh10),
+//   Y_V = i conj(Sh01 - Sh10);
+//   dchi^2/dG_p = 2 w R G_q S^H, dchi^2/dG_q = 2 w R^H G_p S  (complex
+//   gradient d/dRe + i d/dIm).
+template <typename T, typename T2>
+__device__ __forceinline__ void grad_terms(const T2 *V, const T2 *Sm, const T2 *D, T w, const T2 *gp, const T2 *gq,
+                                           T2 *Y, T2 *dGp, T2 *dGq) {
+    T2 R[4], Sh[4], tmp[4], gh[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        R[c] = csub(V[c], D[c]);
+        R[c].x *= 2 * w;
+        R[c].y *= 2 * w;
+    }
+    mherm(gp, gh);
+    mmul(gh, R, tmp);
+    mmul(tmp, gq, Sh);
+    Y[0] = cconj(cadd(Sh[0], Sh[3]));
+    Y[1] = cconj(csub(Sh[0], Sh[3]));
+    Y[2] = cconj(cadd(Sh[1], Sh[2]));
+    T2 d = csub(Sh[1], Sh[2]);
+    Y[3].x = d.y;
+    Y[3].y = d.x;
+    T2 sh[4];
+    mherm(Sm, sh);
+    mmul(R, gq, tmp);
+    mmul(tmp, sh, dGp);
+    mherm(R, gh);
+    mmul(gh, gp, tmp);
+    mmul(tmp, Sm, dGq);
+}
+
 namespace f32 {
 // Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
 // nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small

@@ -275,7 +275,8 @@ cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, lon
 constexpr int NARROW_MAX_NA = 45;      // it takes arrays of up to this many antennas (990 baselines)
 constexpr int NARROW_AUTO_NA_F32 = 32; // RIME_KERNEL_AUTO picks it up to here in FP32 (FP64: 45)
 bool narrow_applies(const rime_ctx *c);
-cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1);
+cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1,
+                          void *yout = nullptr, double *grad_gains = nullptr);
 // the same with prepared parameters over timesteps [P.t_begin, P.t_begin + nt)
 cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt);
 // predict (chi2 = false) or chi^2 over all sources with the kernel that suits the array

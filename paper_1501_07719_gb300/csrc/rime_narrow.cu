@@ -73,12 +73,13 @@ static Shape shape_for(int na, int nchan) {
 }
 
 template <typename T>
-static size_t smem_bytes(int na, int cg) {
+static size_t smem_bytes(int na, int cg, bool grad) {
     using C = Cfg<T>;
     return (size_t)cg * C::SC * na * sizeof(typename C::T2)      // K (times E) per (channel, source, antenna)
            + (size_t)cg * C::SC * sizeof(typename C::T4)         // scaled Stokes per (channel, source)
            + (size_t)C::SC * sizeof(typename C::T4)              // Gaussian coefficients per source
-           + 32 * sizeof(double);                                // reduction scratch
+           + 32 * sizeof(double)                                 // reduction scratch
+           + (grad ? (size_t)cg * na * 8 * sizeof(double) : 0);  // gains gradient per (channel, antenna)
 }
 
 // K = exp(2 pi i nu tau) for the delay stored for (t, s, a).
@@ -121,13 +122,14 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
     using T4 = typename C::T4;
     using Chan = typename C::Chan;
     constexpr int SC = C::SC;
-    constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT;
+    constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int na = P.na;
     T2 *sA = reinterpret_cast<T2 *>(smem_raw);                       // [cg][SC][na]
     T4 *sSt = reinterpret_cast<T4 *>(sA + (size_t)cg * SC * na);     // [cg][SC]
     T4 *sG = sSt + cg * SC;                                          // [SC]
     double *sRed = reinterpret_cast<double *>(sG + SC);              // [32]
+    double *sGG = sRed + 32;                                         // gradient mode: [cg][na][8]
     __shared__ int sLast;
 
     if (inputs_bad(P.status)) return;
@@ -186,6 +188,9 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
     for (int i = 0; i < M; i++)
 #pragma unroll
         for (int c = 0; c < 8; c++) acc[i][c] = T(0);
+    if constexpr (GRAD) {
+        for (int i = tid; i < cg * na * 8; i += THREADS) sGG[i] = 0.0;   // ordered by the first barrier below
+    }
 
     const auto *tau = reinterpret_cast<const typename std::conditional<sizeof(T) == 4, float2, double>::type *>(P.tau);
     const T *rho = reinterpret_cast<const T *>(P.rho);
@@ -297,6 +302,34 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
             }
             const T w = P.has_weight ? weight[row] : T(1);
             chi += (double)(w * r2);
+            if constexpr (GRAD) {
+                // the Stokes-projected adjoint of this visibility and its gains
+                // gradient (eq. 7 through eq. 1), as the tiled kernel's gradient mode
+                T2 D[4], Y[4], dGp[4], dGq[4];
+#pragma unroll
+                for (int c = 0; c < 4; c++) D[c] = data[4 * row + c];
+                grad_terms<T, T2>(V, Sm, D, w, gp, gq, Y, dGp, dGq);
+                T2 *yo = reinterpret_cast<T2 *>(P.yout) + 4 * row;
+#pragma unroll
+                for (int c = 0; c < 4; c++) yo[c] = Y[c];
+                if (P.grad_gains) {
+                    double *gpp = sGG + ((k - k0) * na + p) * 8, *gqq = sGG + ((k - k0) * na + q) * 8;
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        atomicAdd(gpp + 2 * c, (double)dGp[c].x);
+                        atomicAdd(gpp + 2 * c + 1, (double)dGp[c].y);
+                        atomicAdd(gqq + 2 * c, (double)dGq[c].x);
+                        atomicAdd(gqq + 2 * c + 1, (double)dGq[c].y);
+                    }
+                }
+            }
+        }
+    }
+    if constexpr (GRAD) {
+        __syncthreads();
+        for (int i = tid; P.grad_gains && i < ncg * na * 8; i += THREADS) {
+            const int ca = i >> 3, c = ca / na, a = ca - c * na;
+            atomicAdd(&P.grad_gains[8 * (((long long)t * na + a) * P.nchan + k0 + c) + (i & 7)], sGG[i]);
         }
     }
     if constexpr (CHI2) {
@@ -308,7 +341,9 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
 template <typename T, int M, int NT>
 static cudaError_t launch_t(const FusedParams &P, int mode, const Shape &s, int blocks, size_t smem,
                             cudaStream_t stream) {
-    auto kern = mode == MODE_PREDICT ? k_narrow<T, M, NT, MODE_PREDICT> : k_narrow<T, M, NT, MODE_CHI2>;
+    auto kern = mode == MODE_PREDICT ? k_narrow<T, M, NT, MODE_PREDICT>
+                : mode == MODE_CHI2  ? k_narrow<T, M, NT, MODE_CHI2>
+                                     : k_narrow<T, M, NT, MODE_GRAD>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -336,9 +371,10 @@ bool narrow_applies(const rime_ctx *c) {
     return c->dims.na <= (c->dims.precision == RIME_FP64 ? NARROW_MAX_NA : NARROW_AUTO_NA_F32);
 }
 
-cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1) {
+cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1, void *yout,
+                          double *grad_gains) {
     FusedParams P{};
-    fill_fused_params(c, P, vis_out, result, nullptr, nullptr);
+    fill_fused_params(c, P, vis_out, result, yout, grad_gains);
     P.src0 = src0;
     P.src1 = src1;
     return launch_narrow_params(c, mode, P, c->dims.ntime);
@@ -351,7 +387,8 @@ cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, in
     if (blocks == 0) return cudaSuccess;
     if (blocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // cannot happen: <= fused blocks
     const bool f64 = c->dims.precision == RIME_FP64;
-    const size_t smem = f64 ? smem_bytes<double>(c->dims.na, s.cg) : smem_bytes<float>(c->dims.na, s.cg);
+    const bool grad = mode == MODE_GRAD;
+    const size_t smem = f64 ? smem_bytes<double>(c->dims.na, s.cg, grad) : smem_bytes<float>(c->dims.na, s.cg, grad);
     if (f64) return launch_shape<double>(P, mode, s, (int)blocks, smem, c->stream);
     return launch_shape<float>(P, mode, s, (int)blocks, smem, c->stream);
 }
