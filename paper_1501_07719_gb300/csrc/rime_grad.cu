@@ -377,7 +377,11 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
 __device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 pdup(float a) { return make_float2(a, a); }
 
+template <bool GENERAL>
 __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams P) {
+    // GENERAL = false: eq. 4's cos^3 beam, points and Gaussians (the code of
+    // the general case costs this register-bound kernel ~3 %)
+    const int beam_model = GENERAL ? reinterpret_cast<const ChanF *>(P.chan)[0].beam : RIME_BEAM_COS3;
     using T = float;
     using T2 = float2;
     constexpr int SG = GCfg<float>::SG, NP = SG / 2, NG = GTHREADS / NP;
@@ -439,10 +443,10 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
         sact[h] = s < P.nsrc;
         sidx[h] = sact[h] ? s : P.nsrc - 1;
         is_gauss[h] = reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] != T(0);
-        is_disk[h] = P.has_disk && reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] > T(1.5);
+        is_disk[h] = GENERAL && P.has_disk && reinterpret_cast<const T *>(P.gauss)[4 * sidx[h] + 3] > T(1.5);
     }
     const bool any_gauss = is_gauss[0] || is_gauss[1];
-    const bool any_disk = is_disk[0] || is_disk[1];
+    const bool any_disk = GENERAL && (is_disk[0] || is_disk[1]);
     const float4 st0 = reinterpret_cast<const float4 *>(P.stokes)[sidx[0]];
     const float4 st1 = reinterpret_cast<const float4 *>(P.stokes)[sidx[1]];
     const float2 sI = pf2(st0.x, st1.x), sQ = pf2(st0.y, st1.y);
@@ -450,11 +454,14 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     const double *ptab = pointing ? P.pointing + 2 * (long long)t * P.na : nullptr;
     const T2 *yin = reinterpret_cast<const T2 *>(P.yin);
 
-    double out[2][NGRAD];
+    // per-block sums over the block's channels in FP32 (at most 8 terms each;
+    // FP64 adds at 1/64 of the FP32 rate kept the FP64 pipe 11 % busy); the
+    // block partials are combined in FP64
+    float out[2][NGRAD];
 #pragma unroll
     for (int h = 0; h < 2; h++)
 #pragma unroll
-        for (int i = 0; i < NGRAD; i++) out[h][i] = 0.0;
+        for (int i = 0; i < NGRAD; i++) out[h][i] = 0.f;
 
     const int nchunk = (nb + BLC - 1) / BLC;
     auto issue_y = [&](int j) {
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
                 const T *exq = reinterpret_cast<const T *>(P.extra) + 8 * src;
                 T E, t3;
-                beam_Ed(ch.beam, ch.cnu * rRho[i], E, t3);
+                beam_Ed(beam_model, ch.cnu * rRho[i], E, t3);
                 v.x *= E;
                 v.y *= E;
                 T2 d;
@@ -583,29 +590,29 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
             T dlnE2_l = 0, dlnE2_m = 0;
             if (!pointing) {
                 T E, t3;
-                beam_Ed(ch.beam, ch.cnu * rRho[2 * sp + h], E, t3);
+                beam_Ed(beam_model, ch.cnu * rRho[2 * sp + h], E, t3);
                 w *= E * E;
                 const T cnu2 = ch.cnu * ch.cnu;
                 dlnE2_l = T(2) * t3 * cnu2 * l;
                 dlnE2_m = T(2) * t3 * cnu2 * m;
             }
             const T aR = st.x * a[0] + st.y * a[1] + st.z * a[2] + st.w * a[3];
-            out[h][0] += (double)(w * (-k2pi * (a[4] - l_n * a[6]) + (pointing ? a[10] : aR * dlnE2_l)));
-            out[h][1] += (double)(w * (-k2pi * (a[5] - m_n * a[6]) + (pointing ? a[11] : aR * dlnE2_m)));
-            out[h][2] += (double)(w * a[0]);
-            out[h][3] += (double)(w * a[1]);
-            out[h][4] += (double)(w * a[2]);
-            out[h][5] += (double)(w * a[3]);
-            out[h][6] += (double)(w * aR * lnr);
+            out[h][0] += (w * (-k2pi * (a[4] - l_n * a[6]) + (pointing ? a[10] : aR * dlnE2_l)));
+            out[h][1] += (w * (-k2pi * (a[5] - m_n * a[6]) + (pointing ? a[11] : aR * dlnE2_m)));
+            out[h][2] += (w * a[0]);
+            out[h][3] += (w * a[1]);
+            out[h][4] += (w * a[2]);
+            out[h][5] += (w * a[3]);
+            out[h][6] += (w * aR * lnr);
             if (is_gauss[h]) {
                 const T K = is_disk[h] ? T(-4.0 * kPi * kPi / (kCLight * kCLight)) * nu * nu
                                        : T(kGaussK / (kCLight * kCLight)) * nu * nu;
                 const T mj = ex[4], mi = ex[5], sps = ex[6], cps = ex[7];
                 const T dd = mj * mj - mi * mi;
                 const T Au = a[7], Auv = a[8], Av = a[9];
-                out[h][7] += (double)(w * -K * (2 * mj * sps * sps * Au + 4 * mj * sps * cps * Auv + 2 * mj * cps * cps * Av));
-                out[h][8] += (double)(w * -K * (2 * mi * cps * cps * Au - 4 * mi * sps * cps * Auv + 2 * mi * sps * sps * Av));
-                out[h][9] += (double)(w * -K * (2 * sps * cps * dd * Au + 2 * dd * (cps * cps - sps * sps) * Auv -
+                out[h][7] += (w * -K * (2 * mj * sps * sps * Au + 4 * mj * sps * cps * Auv + 2 * mj * cps * cps * Av));
+                out[h][8] += (w * -K * (2 * mi * cps * cps * Au - 4 * mi * sps * cps * Auv + 2 * mi * sps * sps * Av));
+                out[h][9] += (w * -K * (2 * sps * cps * dd * Au + 2 * dd * (cps * cps - sps * sps) * Auv -
                                                 2 * sps * cps * dd * Av));
             }
         }
@@ -741,9 +748,10 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
         k_grad_src<double><<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     } else {
         const size_t smem = GSmem<float>::bytes(c->has_pointing);
-        e = cudaFuncSetAttribute(k_grad_src_f32x2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = (c->beam_model != RIME_BEAM_COS3 || c->has_kind) ? k_grad_src_f32x2<true> : k_grad_src_f32x2<false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_grad_src_f32x2<<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
+        kern<<<(unsigned)blocks, GTHREADS, smem, c->stream>>>(P);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
