@@ -230,6 +230,41 @@ rime_status rime_chi2_streamed(rime_ctx *ctx, const void *data, const void *weig
  * kernel per chunk, at most ntime. 0 for a NULL context. */
 int32_t rime_stream_chunk_ntime(const rime_ctx *ctx);
 
+/* Chains: per-chain residuals for a sampler whose proposals move a few
+ * sources at a time (the BIRO loop of Sec. 2.3 with Metropolis moves).
+ * Chain c keeps N_c = D - V_c in device memory (V_c: the model visibilities
+ * of the chain's current sky model; nchains * ntime * nbl * nchan * 4
+ * complex values). Because eqs. 1-2 are linear in the Stokes vector, a
+ * proposal that gives m sources new values changes the model by the
+ * visibilities dV of a 2m-source sky model (the new values, and the current
+ * values with the Stokes vector negated), and its chi^2 (eq. 7) is
+ * sum w |dV - N_c|^2: the fused predict + chi^2 of 2m sources against N_c.
+ * The chains use the direct kernels; they need static brightness. In FP32
+ * the residuals gather rounding over many accepted moves (about 1e-7 of the
+ * visibilities per move); rime_chains_init starts them afresh. */
+
+/* Starts nchains chains at the context's sky model: N_c = D - V for all c.
+ * Needs data and sources; allocates the residuals (RIME_E_OOM if they do not
+ * fit). Does not wait. */
+rime_status rime_chains_init(rime_ctx *ctx, int32_t nchains);
+
+/* Evaluates one proposal per chain.
+ *   nmove     sources moved per chain, >= 1
+ *   proposed  nchains * nmove sources: chain c's new values of its moved
+ *             sources are sources c*nmove .. c*nmove + nmove - 1
+ *   current   the same sources' current values, in the same order (both
+ *             give shape and kind, or both omit them)
+ *   chi2_dev  device [nchains]: chi^2 of each chain's proposed sky model
+ * The staged pairs become the context's sky model (rime_set_sources), which
+ * rime_chains_accept then reads. Does not wait. */
+rime_status rime_chains_propose(rime_ctx *ctx, int32_t nmove, const rime_sources *proposed,
+                                const rime_sources *current, double *chi2_dev);
+
+/* Applies the last proposal of the chains with accept[c] != 0 (host array
+ * [nchains]): N_c -= dV_c. The caller records the accepted values as the
+ * chains' current ones. Does not wait. */
+rime_status rime_chains_accept(rime_ctx *ctx, const int32_t *accept);
+
 /* Primary beam models E(x), x = beam_c * nu[GHz] * rho, rho the distance of
  * the source from the antenna's pointing centre (rime_set_beam). */
 typedef enum {

@@ -79,10 +79,14 @@ def lib():
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
         L.rime_set_kernel.argtypes = [vp, C.c_int32]
         L.rime_set_beam.argtypes = [vp, C.c_int32, C.c_double]
+        L.rime_chains_init.argtypes = [vp, C.c_int32]
+        L.rime_chains_propose.argtypes = [vp, C.c_int32, C.POINTER(rime_sources), C.POINTER(rime_sources), vp]
+        L.rime_chains_accept.argtypes = [vp, vp]
         L.rime_chi2_streamed.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
         L.rime_stream_chunk_ntime.argtypes, L.rime_stream_chunk_ntime.restype = [vp], C.c_int32
         for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
-                  "rime_set_kernel", "rime_chi2_streamed", "rime_set_beam"):
+                  "rime_set_kernel", "rime_chi2_streamed", "rime_set_beam", "rime_chains_init",
+                  "rime_chains_propose", "rime_chains_accept"):
             getattr(L, f).restype = ip
         for f in ("rime_create", "rime_set_uvw", "rime_set_data", "rime_set_gains",
                   "rime_set_sources", "rime_predict", "rime_chi2", "rime_chi2_async", "rime_chi2_grad",
@@ -315,6 +319,28 @@ def rime_stream_chunk_ntime(ctx) -> int:
 def rime_set_beam(ctx, model: int, beam_c: float):
     """RIME_BEAM_COS3 (eq. 4) or RIME_BEAM_JINC, with the constant C (rad^-1 GHz^-1)."""
     _check(lib().rime_set_beam(ctx, int(model), float(beam_c)), ctx)
+
+
+def rime_chains_init(ctx, nchains: int):
+    """Per-chain residuals N_c = D - V for nchains chains at the context's sky model."""
+    _check(lib().rime_chains_init(ctx, int(nchains)), ctx)
+
+
+def rime_chains_propose(ctx, nmove: int, proposed: dict, current: dict, chi2_dev):
+    """chi^2 of each chain's proposal: proposed / current are SoA source dicts of
+    nchains * nmove sources (chain c: rows c*nmove .. c*nmove + nmove - 1)."""
+    k = _Keep()
+    p = make_sources(proposed["lm"], proposed["stokes"], proposed["alpha"], proposed.get("shape"), k,
+                     proposed.get("kind"))
+    c = make_sources(current["lm"], current["stokes"], current["alpha"], current.get("shape"), k,
+                     current.get("kind"))
+    _check(lib().rime_chains_propose(ctx, int(nmove), C.byref(p), C.byref(c), chi2_dev.data_ptr()), ctx)
+
+
+def rime_chains_accept(ctx, accept):
+    """accept: [nchains] flags (host); applies the last proposal of those chains."""
+    a = np.ascontiguousarray(accept, dtype=np.int32)
+    _check(lib().rime_chains_accept(ctx, a.ctypes.data), ctx)
 
 
 def rime_set_kernel(ctx, kernel: int):

@@ -98,6 +98,22 @@ class Rime:
         (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32) or the direct sum (RIME_TC_OFF)."""
         A.rime_set_tensor_mode(self.ctx, mode)
 
+    def chains_init(self, nchains: int):
+        """Per-chain residuals D - V at the current sky model (rime_chains_init)."""
+        A.rime_chains_init(self.ctx, nchains)
+        self.nchains = int(nchains)
+
+    def chains_propose(self, nmove: int, proposed: dict, current: dict, out=None):
+        """chi^2 of each chain's proposal as a float64 device tensor [nchains];
+        does not wait."""
+        if out is None:
+            out = self.torch.empty(self.nchains, dtype=self.torch.float64, device="cuda")
+        A.rime_chains_propose(self.ctx, nmove, proposed, current, out)
+        return out
+
+    def chains_accept(self, accept):
+        A.rime_chains_accept(self.ctx, accept)
+
     def set_beam(self, model: int, beam_c: float):
         """Beam model of eq. 4's E: RIME_BEAM_COS3 (default) or RIME_BEAM_JINC,
         with its constant C in rad^-1 GHz^-1."""

@@ -65,7 +65,8 @@ void free_all(rime_ctx *c) {
                     c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho, c->d_units,
                     c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
                     c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
-                    c->d_spart, c->d_scounter, c->d_sscale, c->d_sbuf[0], c->d_sbuf[1], c->d_schi};
+                    c->d_spart, c->d_scounter, c->d_sscale, c->d_sbuf[0], c->d_sbuf[1], c->d_schi,
+                    c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     cudaEvent_t evs[] = {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]};

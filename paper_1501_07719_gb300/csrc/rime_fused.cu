@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
     const int t = P.t_begin + rest / P.nchan;
-    const double bsum = fused_item<MODE, GENERAL>(P, S, t, k, u, 0, P.nsrc);
+    const double bsum = fused_item<MODE, GENERAL>(P, S, t, k, u, P.src0, P.src1);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
 }
 
@@ -922,28 +922,29 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
     return launch_tiled_params(c, mode, P, fused_blocks(c));
 }
 
-cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long nblocks) {
+cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long nblocks, cudaStream_t stream) {
+    if (!stream) stream = c->stream;
     if (nblocks == 0) return cudaSuccess;
     if (nblocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // one partial per block
     const int blocks = (int)nblocks;
     if (c->dims.precision == RIME_FP64) {
         size_t sm = f64::smem_bytes();
         switch (mode) {
-            case MODE_PREDICT: return launch_k(f64::k_fused_f64<MODE_PREDICT>, P, blocks, f64::THREADS, sm, c->stream);
-            case MODE_CHI2: return launch_k(f64::k_fused_f64<MODE_CHI2>, P, blocks, f64::THREADS, sm, c->stream);
-            default: return launch_k(f64::k_fused_f64<MODE_GRAD>, P, blocks, f64::THREADS, sm, c->stream);
+            case MODE_PREDICT: return launch_k(f64::k_fused_f64<MODE_PREDICT>, P, blocks, f64::THREADS, sm, stream);
+            case MODE_CHI2: return launch_k(f64::k_fused_f64<MODE_CHI2>, P, blocks, f64::THREADS, sm, stream);
+            default: return launch_k(f64::k_fused_f64<MODE_GRAD>, P, blocks, f64::THREADS, sm, stream);
         }
     }
     size_t sm = sizeof(f32::Smem);
     if (c->beam_model != RIME_BEAM_COS3 || c->has_kind) switch (mode) {
-            case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, true>, P, blocks, f32::THREADS, sm, c->stream);
-            case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, true>, P, blocks, f32::THREADS, sm, c->stream);
-            default: return launch_k(f32::k_fused_f32<MODE_GRAD, true>, P, blocks, f32::THREADS, sm, c->stream);
+            case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, true>, P, blocks, f32::THREADS, sm, stream);
+            case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, true>, P, blocks, f32::THREADS, sm, stream);
+            default: return launch_k(f32::k_fused_f32<MODE_GRAD, true>, P, blocks, f32::THREADS, sm, stream);
         }
     switch (mode) {
-        case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, false>, P, blocks, f32::THREADS, sm, c->stream);
-        case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, false>, P, blocks, f32::THREADS, sm, c->stream);
-        default: return launch_k(f32::k_fused_f32<MODE_GRAD, false>, P, blocks, f32::THREADS, sm, c->stream);
+        case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, false>, P, blocks, f32::THREADS, sm, stream);
+        case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, false>, P, blocks, f32::THREADS, sm, stream);
+        default: return launch_k(f32::k_fused_f32<MODE_GRAD, false>, P, blocks, f32::THREADS, sm, stream);
     }
 }
 

@@ -120,7 +120,7 @@ struct FusedParams {
     // gradient mode only
     void *yout;                // complex T [ntime][nbl][nchan][4]: Stokes-projected adjoint Y_X
     double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
-    int src0, src1;            // FP64 kernel: the source range [src0, src1) of this launch
+    int src0, src1;            // the source range [src0, src1) of this launch (default: all)
     int t_begin;               // first timestep of the launch (the grid covers a time range)
 };
 
@@ -223,6 +223,14 @@ struct rime_ctx {
     int tc_mode = 0;                  // rime_tc_mode
     int kernel = 0;                   // rime_kernel
     int beam_model = 0;               // rime_beam
+    // chains (rime_chains.cu): per-chain residuals N_c = D - V_c
+    int chains_n = 0, chains_move = 0;       // chains; sources moved per chain by the last proposal
+    void *d_chainN = nullptr;                // [chains][ntime][nbl][nchan][4] complex
+    void *d_chain_scratch = nullptr;         // one chain's visibilities
+    double *d_pair = nullptr;                // staged proposal sky model (FP64 parameters)
+    size_t pair_cap = 0;                     // sources it holds
+    int32_t *d_pair_kind = nullptr;
+    double *d_chain_part = nullptr;          // [chains][ntime][blocks]: proposal chi^2 partials
     // streamed chi^2 (rime_stream.cu): a copy stream, two chunk buffers
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
@@ -270,7 +278,9 @@ cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *resu
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
                        double *grad_gains);
 // launches the tiled fused kernel of `mode` with prepared parameters over `blocks` blocks
-cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long blocks);
+// (stream: nullptr = the context's stream)
+cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long blocks,
+                                cudaStream_t stream = nullptr);
 // rime_narrow.cu: the small-array kernel (one thread per baseline and channel)
 constexpr int NARROW_MAX_NA = 45;      // it takes arrays of up to this many antennas (990 baselines)
 constexpr int NARROW_AUTO_NA_F32 = 32; // RIME_KERNEL_AUTO picks it up to here in FP32 (FP64: 45)
@@ -278,7 +288,8 @@ bool narrow_applies(const rime_ctx *c);
 cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1,
                           void *yout = nullptr, double *grad_gains = nullptr);
 // the same with prepared parameters over timesteps [P.t_begin, P.t_begin + nt)
-cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt);
+cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt,
+                                 cudaStream_t stream = nullptr);
 // predict (chi2 = false) or chi^2 over all sources with the kernel that suits the array
 cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool chi2);
 // rime_split.cu

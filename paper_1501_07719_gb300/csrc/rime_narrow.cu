@@ -380,7 +380,8 @@ cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, 
     return launch_narrow_params(c, mode, P, c->dims.ntime);
 }
 
-cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt) {
+cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt, cudaStream_t stream) {
+    if (!stream) stream = c->stream;
     using namespace narrow;
     const Shape s = shape_for(c->dims.na, c->dims.nchan);
     const long long blocks = (long long)nt * s.ngroups;
@@ -389,8 +390,8 @@ cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, in
     const bool f64 = c->dims.precision == RIME_FP64;
     const bool grad = mode == MODE_GRAD;
     const size_t smem = f64 ? smem_bytes<double>(c->dims.na, s.cg, grad) : smem_bytes<float>(c->dims.na, s.cg, grad);
-    if (f64) return launch_shape<double>(P, mode, s, (int)blocks, smem, c->stream);
-    return launch_shape<float>(P, mode, s, (int)blocks, smem, c->stream);
+    if (f64) return launch_shape<double>(P, mode, s, (int)blocks, smem, stream);
+    return launch_shape<float>(P, mode, s, (int)blocks, smem, stream);
 }
 
 cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool chi2) {

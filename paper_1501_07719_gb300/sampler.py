@@ -9,7 +9,10 @@ Metropolis proposal is accepted with probability min(1, exp(-(chi2' - chi2)
 
 * ``EnsembleMetropolis``: K independent random-walk Metropolis chains; the K
   proposals of one step are scored by one batched chi^2 call
-  (``rime_chi2_batched``), so a sampler iteration is one persistent launch.
+  (``rime_chi2_batched``), so a sampler iteration is one persistent launch;
+  or, with ``delta=True``, against per-chain residuals kept on the GPU
+  (``rime_chains_*``): a proposal then costs the predict of the moved
+  sources only.
 * ``fit_map``: maximum-likelihood fit of the sky model by L-BFGS on the
   adjoint gradient (``RimeChi2``, ``rime_chi2_grad``).
 """
@@ -39,10 +42,13 @@ class EnsembleMetropolis:
              outside are rejected without evaluation
     chi2_fn: optional replacement scorer, f(list of K sky models) -> [K]
              chi^2 (by default one batched call on `rime`)
+    delta:   score each proposal as a change of the moved sources (those
+             with a non-zero step) against the chain's residual D - V held on
+             the GPU (rime_chains_*), instead of the whole sky model
     """
 
     def __init__(self, rime, sources: dict, nchains: int, steps: dict, seed: int, bounds: dict | None = None,
-                 chi2_fn=None):
+                 chi2_fn=None, delta: bool = False):
         self.rime = rime
         self.K = int(nchains)
         self.base = {k: np.array(v, dtype=np.float64) for k, v in sources.items() if v is not None}
@@ -57,7 +63,19 @@ class EnsembleMetropolis:
         self.rng = np.random.default_rng(seed)
         self.chi2_fn = chi2_fn or self._batched_chi2
         self.theta = {p: np.tile(self._get(self.base, p), (self.K, 1)) for p in self.steps}
-        self.chi2 = np.asarray(self.chi2_fn([self._model(i, self.theta) for i in range(self.K)]), dtype=np.float64)
+        self.delta = bool(delta)
+        if self.delta:
+            if rime is None or chi2_fn is not None:
+                raise ValueError("delta scoring needs the GPU context and no replacement scorer")
+            # the sources a proposal moves: those with a non-zero step
+            self.moved = np.flatnonzero(np.any([self.steps[p] != 0 for p in self.steps], axis=0))
+            rime.set_sources(self.base)
+            chi0 = rime.chi2()
+            rime.chains_init(self.K)
+            self.chi2 = np.full(self.K, chi0)
+        else:
+            self.chi2 = np.asarray(self.chi2_fn([self._model(i, self.theta) for i in range(self.K)]),
+                                   dtype=np.float64)
         self.naccept = np.zeros(self.K, dtype=np.int64)
         self.nstep = 0
 
@@ -95,6 +113,28 @@ class EnsembleMetropolis:
             ok &= np.all(l * l + m * m < 1.0, axis=1)
         return ok
 
+    def _moved_rows(self, theta: dict) -> dict:
+        """The moved sources of every chain under theta, chain-major
+        ([K * m] rows), as a sky-model dict."""
+        out = {}
+        for key, v in self.base.items():
+            rows = np.repeat(v[self.moved][None], self.K, axis=0)   # [K, m, ...]
+            out[key] = rows
+        for p, vals in theta.items():
+            key, col = PARAMS[p]
+            if col is None:
+                out[key][:, :] = vals[:, self.moved]
+            else:
+                out[key][:, :, col] = vals[:, self.moved]
+        return {k: np.ascontiguousarray(v.reshape((-1,) + v.shape[2:])) for k, v in out.items()}
+
+    def _delta_chi2(self, prop: dict, ok: np.ndarray) -> np.ndarray:
+        # chains whose proposal left the prior's support propose no change
+        safe = {p: np.where(ok[:, None], prop[p], self.theta[p]) for p in prop}
+        out = self.rime.chains_propose(len(self.moved), self._moved_rows(safe), self._moved_rows(self.theta))
+        self.rime.sync()
+        return out.cpu().numpy()
+
     def step(self) -> np.ndarray:
         """One Metropolis step of every chain; returns which chains accepted."""
         prop = {p: self.theta[p] + self.steps[p] * self.rng.standard_normal((self.K, self.nsrc))
@@ -103,9 +143,14 @@ class EnsembleMetropolis:
         ok = self._in_bounds(prop)
         chi2p = np.full(self.K, np.inf)
         idx = np.flatnonzero(ok)
-        if idx.size:
+        if self.delta:
+            if idx.size:
+                chi2p[idx] = self._delta_chi2(prop, ok)[idx]
+        elif idx.size:
             chi2p[idx] = self.chi2_fn([self._model(i, prop) for i in idx])
         accept = ok & (log_u < -0.5 * (chi2p - self.chi2))
+        if self.delta and accept.any():
+            self.rime.chains_accept(accept.astype(np.int32))
         for p in self.steps:
             self.theta[p][accept] = prop[p][accept]
         self.chi2[accept] = chi2p[accept]

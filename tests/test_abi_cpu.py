@@ -80,6 +80,9 @@ def test_null_context_calls_are_rejected(L):
     assert L.rime_set_batched_config(None, None) == 1
     assert L.rime_set_kernel(None, 0) == 1
     assert L.rime_set_beam(None, 0, 65.0) == 1
+    assert L.rime_chains_init(None, 4) == 1
+    assert L.rime_chains_propose(None, 1, None, None, None) == 1
+    assert L.rime_chains_accept(None, None) == 1
     assert L.rime_chi2_streamed(None, None, None, 0, None) == 1
     assert L.rime_stream_chunk_ntime(None) == 0
     assert L.rime_set_tensor_mode(None, 0) == 1
