@@ -487,6 +487,19 @@ def run_only(args):
         ctx.set_tensor_mode({"chi2": R.RIME_TC_OFF, "split-bf16": R.RIME_TC_SPLIT_BF16,
                              "split-tf32": R.RIME_TC_SPLIT_TF32}[args.only])
         fn = lambda: ctx.chi2_async(out)
+    elif args.only == "chains":
+        # 128 chains, each proposing a move of the brightest source against
+        # its resident residual (rime_chains_propose)
+        K = 128
+        ctx.chains_init(K)
+        j = int(np.argmax(inp["sources"]["stokes"][:, 0]))
+        cur = {k: np.repeat(v[j:j + 1], K, axis=0) for k, v in inp["sources"].items()}
+        rng = np.random.default_rng(0)
+        prop = {k: v.copy() for k, v in cur.items()}
+        prop["lm"] += rng.normal(0, 1e-8, prop["lm"].shape)
+        prop["stokes"] *= 1 + rng.normal(0, 1e-3, (K, 1))
+        out = torch.zeros(K, dtype=torch.float64, device="cuda")
+        fn = lambda: ctx.chains_propose(1, prop, cur, out=out)
     elif args.only == "grad":
         gs = torch.zeros((wl.nsrc, 10), dtype=torch.float64, device="cuda")
         gg = torch.zeros((wl.ntime, wl.na, wl.nchan, 2, 2), dtype=torch.complex128, device="cuda")
@@ -542,7 +555,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the gradient, batched and split-precision comparisons")
-    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep"],
+    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep", "chains"],
                     help="time one form on --workload (optionally with fewer timesteps / channels) "
                          "instead of the benchmark; for profiling")
     ap.add_argument("--ntime", type=int, default=0)
