@@ -639,6 +639,235 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     }
 }
 
+// Channel-parallel variant for units with few baselines (arrays of up to 23
+// antennas): a block owns (t, CPC channels, unit, CPS sources) and a thread
+// one (source, channel), summing the 12 adjoint moments over all the unit's
+// baselines and forming that channel's 10 gradients (the same formulas as
+// k_grad_src). The baseline-group threads of k_grad_src would each see one
+// or two of a small unit's baselines per channel and walk its channels one
+// after another; here the channels run side by side.
+constexpr int CPS = 16;   // sources per block
+template <typename T> struct CpCfg;
+template <> struct CpCfg<float> { static constexpr int CPC = 16; };    // channels per block
+template <> struct CpCfg<double> { static constexpr int CPC = 8; };
+constexpr int NBCP = 256;   // baselines of a unit, at most
+
+template <typename T>
+struct CpSmem {
+    using T2 = typename GCfg<T>::T2;
+    using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+    static size_t bytes(int nloc, bool pointing) {
+        constexpr int CPC = CpCfg<T>::CPC;
+        size_t b = (size_t)CPS * nloc * (sizeof(TauT) + sizeof(T));           // raw delays, beam radii
+        b += (size_t)CPC * nloc * CPS * sizeof(T2) * (pointing ? 2 : 1);       // A (and dlnE) per channel
+        b += (size_t)NBCP * 4 * sizeof(T);                                     // baseline table
+        b = (b + 7) & ~(size_t)7;
+        b += (size_t)CPC * CPS * NGRAD * sizeof(double);                        // per-thread results
+        return b;
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(CPS * CpCfg<T>::CPC) k_grad_src_cp(const GradParams P) {
+    using C = GCfg<T>;
+    using T2 = typename C::T2;
+    using Chan = typename C::Chan;
+    using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+    constexpr int CPC = CpCfg<T>::CPC, NT = CPS * CPC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (inputs_bad(P.status)) return;
+    const int tid = threadIdx.x;
+    const int sl = tid % CPS, kc = tid / CPS;
+    int bid = blockIdx.x;
+    const int sch = bid % P.nsch;
+    bid /= P.nsch;
+    const int u = bid % P.nunits;
+    bid /= P.nunits;
+    const int cg = bid % P.ncg;
+    const int t = bid / P.ncg;
+    const Unit U = P.units[u];
+    const int nb = U.nbody;
+    const int nloc = U.diag ? U.nr : U.nr + U.nc;
+    TauT *rTau = reinterpret_cast<TauT *>(smem_raw);                  // [nloc][CPS]
+    T *rRho = reinterpret_cast<T *>(rTau + nloc * CPS);               // [nloc][CPS]
+    T2 *sA = reinterpret_cast<T2 *>(rRho + nloc * CPS);               // [CPC][nloc][CPS]
+    const bool pointing = P.has_pointing != 0;
+    T2 *sE = sA + CPC * nloc * CPS;                                   // [CPC][nloc][CPS] with pointing
+    T *sB = reinterpret_cast<T *>(pointing ? sE + CPC * nloc * CPS : sE);
+    double *sRed = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(sB + 4 * NBCP) + 7) & ~(uintptr_t)7);   // [CPC][CPS][NGRAD]
+    const int s = sch * CPS + sl;
+    const bool sact = s < P.nsrc;
+    const int sidx = sact ? s : P.nsrc - 1;
+    const int k0 = cg * P.chan_group;
+    const int k = k0 + kc;
+    const bool kact = kc < P.chan_group && k < P.nchan;
+    const Chan *chan = reinterpret_cast<const Chan *>(P.chan);
+    const double *ptab = pointing ? P.pointing + 2 * (long long)t * P.na : nullptr;
+
+    // ---- delays and radii of every (antenna, source); the baseline table ----
+    for (int i = tid; i < nloc * CPS; i += NT) {
+        const int a = i / CPS, ss = i - a * CPS;
+        const int src = min(sch * CPS + ss, P.nsrc - 1);
+        const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+        const long long di = ((long long)t * P.nsrc + src) * P.na + ant;
+        rTau[i] = reinterpret_cast<const TauT *>(P.tau)[di];
+        rRho[i] = reinterpret_cast<const T *>(P.rho)[di];
+    }
+    const uint16_t *bls = P.bls + U.tile0;
+    for (int i = tid; i < nb; i += NT) {
+        const uint16_t e = bls[i];
+        const int pl = e & 0xff, ql = e >> 8;
+        const int p = U.r0 + pl, q = U.c0 + ql;
+        const double *xp = P.uvw + 3 * ((long long)t * P.na + p);
+        const double *xq = P.uvw + 3 * ((long long)t * P.na + q);
+        const int la = pl, lb = U.diag ? ql : U.nr + ql;
+        T *b = sB + 4 * i;
+        b[0] = (T)(xp[0] - xq[0]);
+        b[1] = (T)(xp[1] - xq[1]);
+        b[2] = (T)(xp[2] - xq[2]);
+        b[3] = int_bits<T>((la * CPS) | ((lb * CPS) << 16));
+    }
+    __syncthreads();
+    // ---- A = K (E K with pointing errors) for every (channel, antenna, source) ----
+    for (int i = tid; i < CPC * nloc * CPS; i += NT) {
+        const int c = i / (nloc * CPS), r = i - c * (nloc * CPS);
+        const int kk = min(k0 + c, P.nchan - 1);
+        const Chan ch = chan[kk];
+        T2 v = phase(rTau + r, 0, ch);
+        if (pointing) {
+            const int a = r / CPS, ss = r - a * CPS;
+            const int src = min(sch * CPS + ss, P.nsrc - 1);
+            const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+            const T *ex = reinterpret_cast<const T *>(P.extra) + 8 * src;
+            T E, t3;
+            beam_Ed(ch.beam, ch.cnu * rRho[r], E, t3);
+            v.x *= E;
+            v.y *= E;
+            T2 d;
+            d.x = t3 * ch.cnu * ch.cnu * (ex[0] - (T)ptab[2 * ant]);
+            d.y = t3 * ch.cnu * ch.cnu * (ex[1] - (T)ptab[2 * ant + 1]);
+            sE[i] = d;
+        }
+        sA[i] = v;
+    }
+    __syncthreads();
+
+    double out[NGRAD];
+#pragma unroll
+    for (int i = 0; i < NGRAD; i++) out[i] = 0.0;
+    if (kact) {
+        const Chan ch = chan[k];
+        const T *st = reinterpret_cast<const T *>(P.stokes) + 4 * sidx;
+        const T sI = st[0], sQ = st[1], sU = st[2], sV = st[3];
+        const T *gq = reinterpret_cast<const T *>(P.gauss) + 4 * sidx;
+        const bool is_gauss = gq[3] != T(0), is_disk = gq[3] > T(1.5);
+        const T gA = gq[0] * ch.nu2, gB = gq[1] * ch.nu2, gC = gq[2] * ch.nu2;
+        const T2 *cA = sA + kc * nloc * CPS, *cE = sE + kc * nloc * CPS;
+        const T2 *yin = reinterpret_cast<const T2 *>(P.yin);
+        T acc[NACC];
+#pragma unroll
+        for (int i = 0; i < NACC; i++) acc[i] = T(0);
+        for (int i = 0; i < nb; i++) {
+            const T *b = sB + 4 * i;
+            const T du = b[0], dv = b[1], dw = b[2];
+            const int pq = bits_int(b[3]);
+            const int oa = pq & 0xffff, ob = pq >> 16;
+            const T2 ap = cA[oa + sl], aq = cA[ob + sl];
+            T zr = ap.x * aq.x + ap.y * aq.y;
+            T zi = ap.y * aq.x - ap.x * aq.y;
+            T hq = T(1);
+            if (is_gauss) {
+                const T e = gA * du * du + gB * du * dv + gC * dv * dv;
+                T g;
+                if (is_disk) {
+                    const T r = rsqrt(T(1) + e);
+                    g = r * r * r;
+                    hq = T(-1.5) * r * r;
+                } else {
+                    g = gexp(e);
+                }
+                zr *= g;
+                zi *= g;
+            }
+            const uint16_t e16 = bls[i];
+            const int p = U.r0 + (e16 & 0xff), q = U.c0 + (e16 >> 8);
+            const long long bl = (long long)p * P.na - (long long)p * (p + 1) / 2 + (q - p - 1);
+            const T2 *y = yin + 4 * (((long long)t * P.nbl + bl) * P.nchan + k);
+            const T2 y0 = y[0], y1 = y[1], y2 = y[2], y3 = y[3];
+            acc[0] += zr * y0.x - zi * y0.y;
+            acc[1] += zr * y1.x - zi * y1.y;
+            acc[2] += zr * y2.x - zi * y2.y;
+            acc[3] += zr * y3.x - zi * y3.y;
+            const T br = sI * y0.x + sQ * y1.x + sU * y2.x + sV * y3.x;
+            const T bi = sI * y0.y + sQ * y1.y + sU * y2.y + sV * y3.y;
+            const T re = zr * br - zi * bi, im = zr * bi + zi * br;
+            acc[4] += im * du;
+            acc[5] += im * dv;
+            acc[6] += im * dw;
+            if (is_gauss) {
+                const T rh = re * hq;
+                acc[7] += rh * du * du;
+                acc[8] += rh * du * dv;
+                acc[9] += rh * dv * dv;
+            }
+            if (pointing) {
+                const T2 ep = cE[oa + sl], eq = cE[ob + sl];
+                acc[10] += re * (ep.x + eq.x);
+                acc[11] += re * (ep.y + eq.y);
+            }
+        }
+        // ---- this channel's factors (as in k_grad_src) ----
+        const T *extra = reinterpret_cast<const T *>(P.extra) + 8 * sidx;
+        const T l = extra[0], m = extra[1], l_n = extra[2], m_n = extra[3];
+        const T nu = nu_of<T>(ch);
+        const T lnr = log(nu / (T)P.ref_freq_hz);
+        T w = exp(reinterpret_cast<const T *>(P.alpha)[sidx] * lnr);
+        T dlnE2_l = 0, dlnE2_m = 0;
+        if (!pointing) {
+            T E, t3;
+            beam_Ed(ch.beam, ch.cnu * rRho[sl], E, t3);
+            w *= E * E;
+            const T cnu2 = ch.cnu * ch.cnu;
+            dlnE2_l = T(2) * t3 * cnu2 * l;
+            dlnE2_m = T(2) * t3 * cnu2 * m;
+        }
+        const T aR = sI * acc[0] + sQ * acc[1] + sU * acc[2] + sV * acc[3];
+        const T k2pi = T(2.0 * kPi / kCLight) * nu;
+        out[0] = (double)(w * (-k2pi * (acc[4] - l_n * acc[6]) + (pointing ? acc[10] : aR * dlnE2_l)));
+        out[1] = (double)(w * (-k2pi * (acc[5] - m_n * acc[6]) + (pointing ? acc[11] : aR * dlnE2_m)));
+        out[2] = (double)(w * acc[0]);
+        out[3] = (double)(w * acc[1]);
+        out[4] = (double)(w * acc[2]);
+        out[5] = (double)(w * acc[3]);
+        out[6] = (double)(w * aR * lnr);
+        if (is_gauss) {
+            const T K = is_disk ? T(-4.0 * kPi * kPi / (kCLight * kCLight)) * nu * nu
+                                : T(kGaussK / (kCLight * kCLight)) * nu * nu;
+            const T mj = extra[4], mi = extra[5], sps = extra[6], cps = extra[7];
+            const T dd = mj * mj - mi * mi;
+            const T Au = acc[7], Auv = acc[8], Av = acc[9];
+            out[7] = (double)(w * -K * (2 * mj * sps * sps * Au + 4 * mj * sps * cps * Auv + 2 * mj * cps * cps * Av));
+            out[8] = (double)(w * -K * (2 * mi * cps * cps * Au - 4 * mi * sps * cps * Auv + 2 * mi * sps * sps * Av));
+            out[9] = (double)(w * -K * (2 * sps * cps * dd * Au + 2 * dd * (cps * cps - sps * sps) * Auv -
+                                        2 * sps * cps * dd * Av));
+        }
+    }
+    // ---- combine the channels in a fixed order: one partial per source ----
+#pragma unroll
+    for (int i = 0; i < NGRAD; i++) sRed[(kc * CPS + sl) * NGRAD + i] = out[i];
+    __syncthreads();
+    if (kc == 0 && sact) {
+        const long long prow = ((long long)t * P.ncg + cg) * P.nunits + u;
+        double *o = P.partials + (prow * P.nsrc + s) * NGRAD;
+        for (int i = 0; i < NGRAD; i++) {
+            double v = 0.0;
+            for (int c = 0; c < CPC; c++) v += sRed[(c * CPS + sl) * NGRAD + i];
+            o[i] = v;
+        }
+    }
+}
+
 // Column sums of a [nrows][ncols] array in fixed order: block (x, y) sums
 // rows [y rpb, (y+1) rpb) of 32 columns with 8 row phases, then the phases.
 constexpr int RTX = 32, RTY = 8;
@@ -696,9 +925,12 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     cudaError_t e = ensure_grad_units(c);
     if (e != cudaSuccess) return e;
     const bool f64 = c->dims.precision == RIME_FP64;
-    const int SG = f64 ? GCfg<double>::SG : GCfg<float>::SG;
+    // units with few baselines (one unit of up to 23 antennas): the
+    // channel-parallel kernel
+    const bool cp = c->dims.na <= 23;
+    const int SG = cp ? CPS : f64 ? GCfg<double>::SG : GCfg<float>::SG;
     const int nsch = (c->nsrc + SG - 1) / SG;
-    const int chan_group = 8;
+    const int chan_group = cp ? (f64 ? CpCfg<double>::CPC : CpCfg<float>::CPC) : 8;
     const int ncg = (c->dims.nchan + chan_group - 1) / chan_group;
     const long long nrows = (long long)c->dims.ntime * ncg * c->ngunits;
     const long long ncols = (long long)c->nsrc * NGRAD;
@@ -741,7 +973,20 @@ cudaError_t launch_grad_src(rime_ctx *c, double *grad_src) {
     P.partials = c->d_gpart;
     P.status = c->d_status;
     const long long blocks = nrows * nsch;
-    if (f64) {
+    if (cp) {
+        const int nloc = c->dims.na;   // one diagonal unit
+        if (f64) {
+            const size_t smem = CpSmem<double>::bytes(nloc, c->has_pointing);
+            e = cudaFuncSetAttribute(k_grad_src_cp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_grad_src_cp<double><<<(unsigned)blocks, CPS * CpCfg<double>::CPC, smem, c->stream>>>(P);
+        } else {
+            const size_t smem = CpSmem<float>::bytes(nloc, c->has_pointing);
+            e = cudaFuncSetAttribute(k_grad_src_cp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_grad_src_cp<float><<<(unsigned)blocks, CPS * CpCfg<float>::CPC, smem, c->stream>>>(P);
+        }
+    } else if (f64) {
         const size_t smem = GSmem<double>::bytes(c->has_pointing);
         e = cudaFuncSetAttribute(k_grad_src<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
