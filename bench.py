@@ -405,9 +405,10 @@ K40_TABLE4_S = {7: (0.0042, 0.0073), 14: (0.0136, 0.0215), 27: (0.0435, 0.0703),
                 128: (0.7007, 0.9113), 192: (1.5730, 2.3540)}
 
 
-def _sweep_time(torch, R, wl, f64, reps):
-    """Median device time (ms) of one fused chi^2 on workload wl; the data are
-    zero and the weights the workload's (the cost does not depend on values)."""
+def _sweep_time(torch, R, wl, f64, reps, grad=False):
+    """Median device time (ms) of one fused chi^2 on workload wl (and, with
+    grad, of one chi^2 + gradient call); the data are zero and the weights
+    the workload's (the cost does not depend on values)."""
     inp = rime_synth.make_inputs(wl, precision="f64" if f64 else "f32", noise=False)
     cdt = torch.complex128 if f64 else torch.complex64
     rdt = np.float64 if f64 else np.float32
@@ -423,6 +424,13 @@ def _sweep_time(torch, R, wl, f64, reps):
         ctx.chi2_async(out)
     ctx.sync()
     ms = _timed(torch, stream, lambda: ctx.chi2_async(out), reps)
+    if grad:
+        gs = torch.zeros((wl.nsrc, 10), dtype=torch.float64, device="cuda")
+        gg = torch.zeros((wl.ntime, wl.na, wl.nchan, 2, 2), dtype=torch.complex128, device="cuda")
+        R.rime_chi2_grad(ctx.ctx, gs, gg)
+        gms = _timed(torch, stream, lambda: R.rime_chi2_grad(ctx.ctx, gs, gg), max(2, reps // 3))
+        ctx.close()
+        return ms, gms
     ctx.close()
     return ms
 
@@ -440,9 +448,15 @@ def form_sweep(torch, R):
         row = {"na": na, "nbl": wl.nbl}
         for i, (name, f64) in enumerate((("f32", False), ("f64", True))):
             reps = 3 if (f64 and na >= 128) else 10
-            ms = _sweep_time(torch, R, wl, f64, reps)
+            if f64:
+                ms = _sweep_time(torch, R, wl, f64, reps)
+            else:
+                ms, gms = _sweep_time(torch, R, wl, f64, reps, grad=True)
             row[name] = {"ms": ms, "terms_per_s": terms_of(wl) / (ms * 1e-3),
                          "k40_s": K40_TABLE4_S[na][i], "speedup_vs_k40": K40_TABLE4_S[na][i] / (ms * 1e-3)}
+            if not f64:
+                row[name]["chi2_grad_ms"] = gms
+                row[name]["grad_over_chi2"] = gms / ms
         rows.append(row)
     base = dict(na=7, ntime=100, nchan=64, npsrc=50, ngsrc=50)
     dims = {"nchan": [64, 128, 256, 512], "ntime": [100, 300, 600, 1000],
