@@ -56,11 +56,15 @@ struct Shape {
     int cg, m, nt, ngroups;
 };
 
-static Shape shape_for(int na, int nchan) {
+static Shape shape_for(int na, int ntime, int nchan, int nsm) {
     const int nbl = na * (na - 1) / 2;
     Shape s;
     if (nbl <= 256) {
         s.cg = std::max(1, std::min(std::min(nchan, CG_MAX), 256 / nbl));
+        // small problems: fewer channels per block, so that the blocks cover
+        // every SM twice (the FP64 pipe of each SM is the limit there)
+        const long long fit = std::max(1LL, (long long)ntime * nchan / (2LL * std::max(nsm, 1)));
+        s.cg = (int)std::min<long long>(s.cg, fit);
         s.m = 1;
         s.nt = 256;
     } else {
@@ -383,7 +387,9 @@ cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, 
 cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt, cudaStream_t stream) {
     if (!stream) stream = c->stream;
     using namespace narrow;
-    const Shape s = shape_for(c->dims.na, c->dims.nchan);
+    if (c->nsm <= 0 && cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->nsm = 152;
+    const Shape s = shape_for(c->dims.na, c->dims.ntime, c->dims.nchan, c->nsm);
     const long long blocks = (long long)nt * s.ngroups;
     if (blocks == 0) return cudaSuccess;
     if (blocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // cannot happen: <= fused blocks
