@@ -217,7 +217,8 @@ rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
  *                lets the copies overlap the kernels; pageable works, without
  *                overlap) or device memory
  *   weight       [ntime][nbl][nchan] real, or NULL (unit weights)
- *   chunk_ntime  timesteps per chunk; <= 0: rime_stream_chunk_ntime(ctx)
+ *   chunk_ntime  timesteps per chunk; <= 0: rime_stream_chunk_ntime(ctx), with a
+ *                first chunk a quarter as long (its copy is not overlapped)
  *   chi2         out: host pointer
  * Waits for the result. Each chunk's data and weights are checked on the GPU
  * as they arrive: NaN/Inf gives RIME_E_NONFINITE, a negative weight

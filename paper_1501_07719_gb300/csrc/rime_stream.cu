@@ -97,7 +97,10 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     if (!c->sources_set) return fail_ctx(c, RIME_E_STATE, "rime_set_sources has not been called");
     const int ntime = c->dims.ntime;
     const int nt = chunk_ntime > 0 ? std::min<int>(chunk_ntime, ntime) : rime_stream_chunk_ntime(c);
-    const int nchunks = (ntime + nt - 1) / nt;
+    // the first chunk's copy is the one no kernel hides: a quarter-length
+    // first chunk (library-chosen lengths only) starts the kernels sooner
+    const int first = chunk_ntime > 0 ? nt : std::max(1, nt / 4);
+    const int nchunks = 1 + (ntime - first + nt - 1) / nt;
     const size_t ts = c->tsize();
     const size_t vis_t = (size_t)c->nbl * c->dims.nchan;           // visibilities per timestep
     const size_t dbytes = vis_t * 8 * ts, wbytes = vis_t * ts;      // per timestep
@@ -111,7 +114,8 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     const char *hw = static_cast<const char *>(weight);
     for (int i = 0; i < nchunks; i++) {
         const int b = i & 1;
-        const int t0 = i * nt, nti = std::min(nt, ntime - t0);
+        const int t0 = i == 0 ? 0 : first + (i - 1) * nt;
+        const int nti = std::min(i == 0 ? first : nt, ntime - t0);
         char *bd = static_cast<char *>(c->d_sbuf[b]);
         char *bw = bd + (size_t)nt * dbytes;
         if (i >= 2) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0), "stream wait");
