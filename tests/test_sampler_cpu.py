@@ -64,3 +64,40 @@ def test_adapt_brings_the_acceptance_rate_near_its_target(start):
 def test_unknown_parameter_is_rejected():
     with pytest.raises(ValueError):
         sampler.EnsembleMetropolis(None, _sky(), 2, {"flux": 1.0}, seed=0, chi2_fn=lambda m: np.zeros(len(m)))
+
+
+def test_delta_scoring_needs_the_gpu_context():
+    # residual-based scoring keeps state on the GPU: no stand-in scorer, no None context
+    with pytest.raises(ValueError):
+        sampler.EnsembleMetropolis(None, _sky(), 2, {"l": 1e-4}, seed=0, delta=True)
+    with pytest.raises(ValueError):
+        sampler.EnsembleMetropolis(object(), _sky(), 2, {"l": 1e-4}, seed=0, delta=True,
+                                   chi2_fn=lambda m: np.zeros(len(m)))
+
+
+def test_moved_rows_are_chain_major_and_carry_the_moved_parameters():
+    class FakeRime:
+        def set_sources(self, src):
+            self.src = src
+
+        def chi2(self):
+            return 1.0
+
+        def chains_init(self, k):
+            self.k = k
+
+    sky = _sky(4)
+    sky["shape"][2] = [2e-5, 1e-5, 0.3]
+    steps = {"l": np.array([0.0, 1e-4, 0.0, 2e-4]), "I": np.array([0.0, 0.1, 0.0, 0.0])}
+    s = sampler.EnsembleMetropolis(FakeRime(), sky, 3, steps, seed=0, delta=True)
+    np.testing.assert_array_equal(s.moved, [1, 3])       # sources with a non-zero step
+    theta = {p: s.theta[p] + np.arange(3)[:, None] * 10.0 for p in s.theta}
+    rows = s._moved_rows(theta)
+    assert rows["lm"].shape == (6, 2) and rows["stokes"].shape == (6, 4) and rows["shape"].shape == (6, 3)
+    for c in range(3):
+        for j, src in enumerate((1, 3)):
+            r = 2 * c + j
+            assert rows["lm"][r, 0] == sky["lm"][src, 0] + 10.0 * c
+            assert rows["lm"][r, 1] == sky["lm"][src, 1]       # m is not moved
+            assert rows["stokes"][r, 0] == sky["stokes"][src, 0] + 10.0 * c
+            np.testing.assert_array_equal(rows["shape"][r], sky["shape"][src])
