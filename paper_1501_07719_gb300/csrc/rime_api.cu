@@ -69,7 +69,7 @@ void free_all(rime_ctx *c) {
                     c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    cudaEvent_t evs[] = {c->ev_start, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]};
+    cudaEvent_t evs[] = {c->ev_start, c->ev_entry, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]};
     for (cudaEvent_t e : evs)
         if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);

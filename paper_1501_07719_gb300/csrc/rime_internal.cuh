@@ -234,6 +234,8 @@ struct rime_ctx {
     // streamed chi^2 (rime_stream.cu): a copy stream, two chunk buffers
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    bool stream_used = false;                // ev_start marks the previous streamed call's end
+    cudaEvent_t ev_entry = nullptr;          // the context's stream at a call with device inputs
     void *d_sbuf[2] = {nullptr, nullptr};   // chunk data, then chunk weights
     size_t sbuf_cap = 0;                     // bytes of each buffer
     double *d_schi = nullptr;                // chi^2 of each chunk

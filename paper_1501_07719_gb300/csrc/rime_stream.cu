@@ -8,7 +8,8 @@
 // on a second stream into buffer i mod 2 while the fused kernel reduces chunk
 // i - 1 on the context's stream. Events order the two streams:
 //   copied[b]  (copy stream)    -> the kernel of the chunk in buffer b may start;
-//   free[b]    (context stream) -> buffer b may be overwritten (two chunks on).
+//   free[b]    (context stream) -> buffer b may be overwritten (two chunks on);
+//   start      (context stream, end of the previous call) -> the buffers are free.
 // Each chunk's data are checked on arrival; each chunk's kernel writes its
 // chi^2 to its own slot, and one thread adds the slots in chunk order, so the
 // result does not depend on the chunking schedule's timing.
@@ -34,7 +35,8 @@ cudaError_t ensure(rime_ctx *c, size_t bytes, int nchunks) {
     if (!c->copy_stream) {
         e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
-        cudaEvent_t *evs[] = {&c->ev_start, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0], &c->ev_free[1]};
+        cudaEvent_t *evs[] = {&c->ev_start, &c->ev_entry, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0],
+                              &c->ev_free[1]};
         for (cudaEvent_t *ev : evs) {
             e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
             if (e != cudaSuccess) return e;
@@ -106,10 +108,24 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     const size_t dbytes = vis_t * 8 * ts, wbytes = vis_t * ts;      // per timestep
     CKS(c, ensure(c, (size_t)nt * std::max(dbytes + wbytes, (size_t)16), nchunks), "allocating chunk buffers");
     CKS(c, reset_status_class(c, EC_SDATA), "reset status");
-    // the copy stream must not overwrite a buffer that earlier work on the
-    // context's stream still reads
-    CKS(c, cudaEventRecord(c->ev_start, c->stream), "event");
-    CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0), "stream wait");
+    // the copy stream must not overwrite a buffer that the previous streamed
+    // call's kernels still read; it need not wait for the rest of the
+    // context's work (uploads of uvw, gains, sources), which the copies overlap
+    if (c->stream_used) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0), "stream wait");
+    // device-memory inputs may be written by work queued on the context's
+    // stream: then the copies follow that work
+    auto on_device = [](const void *p) {
+        cudaPointerAttributes a;
+        if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();   // clear a sticky "invalid value" from an unknown pointer
+            return false;
+        }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    };
+    if (on_device(data) || on_device(weight)) {
+        CKS(c, cudaEventRecord(c->ev_entry, c->stream), "event");
+        CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_entry, 0), "stream wait");
+    }
     const char *hd = static_cast<const char *>(data);
     const char *hw = static_cast<const char *>(weight);
     for (int i = 0; i < nchunks; i++) {
@@ -147,6 +163,8 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     }
     k_sum_in_order<<<1, 32, 0, c->stream>>>(nchunks, c->d_schi, &c->d_status->chi2, c->d_status);
     CKS(c, cudaGetLastError(), "chunk sum");
+    CKS(c, cudaEventRecord(c->ev_start, c->stream), "event");   // the buffers' last readers
+    c->stream_used = true;
     rime_status s = sync_status_ctx(c);
     // streamed data errors belong to this call only
     cudaError_t e = reset_status_class(c, EC_SDATA);
