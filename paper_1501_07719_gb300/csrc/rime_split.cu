@@ -117,21 +117,24 @@ __device__ __forceinline__ uint32_t pack_bf16(float x, float y) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(y), "f"(x));
     return r;
 }
-// x = hi + lo with hi = x rounded to 8 significant bits by Veltkamp's
-// splitting (c = 2^16 + 1; each step rounded separately, no FMA contraction,
-// so hi converts to BF16 without rounding) and lo = x - hi exactly, then
-// rounded to BF16.
-__device__ __forceinline__ float veltkamp_hi8(float x) {
-    const float t = __fmul_rn(x, 65537.0f);
-    return __fsub_rn(t, __fsub_rn(t, x));
-}
+// x = hi + lo with hi = x rounded to nearest BF16 and lo = x - hi, which is
+// exact in FP32 (the error of rounding to 8 significant bits needs at most
+// 16), then rounded to BF16. hi is unpacked from its word by shifts.
 __device__ __forceinline__ void split_bf16(float x, float y, uint32_t &hi, uint32_t &lo) {
-    const float xh = veltkamp_hi8(x), yh = veltkamp_hi8(y);
-    hi = pack_bf16(xh, yh);
+    hi = pack_bf16(x, y);
+    const float xh = __uint_as_float(hi << 16), yh = __uint_as_float(hi & 0xffff0000u);
     lo = pack_bf16(__fsub_rn(x, xh), __fsub_rn(y, yh));
 }
-// (x, y) word -> (-y, x): the same pair multiplied by i
-__device__ __forceinline__ uint32_t rot_bf16(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x00008000u; }
+// split_bf16 and the split words of i (x + i y) = -y + i x, converted
+// directly (rounding commutes with negation).
+__device__ __forceinline__ void split_bf16_rot(float x, float y, uint32_t &hi, uint32_t &lo, uint32_t &hr,
+                                               uint32_t &lr) {
+    hi = pack_bf16(x, y);
+    hr = pack_bf16(-y, x);
+    const float dx = __fsub_rn(x, __uint_as_float(hi << 16)), dy = __fsub_rn(y, __uint_as_float(hi & 0xffff0000u));
+    lo = pack_bf16(dx, dy);
+    lr = pack_bf16(-dy, dx);
+}
 // TF32: round to nearest (ties away) into the 19 bits the tensor core reads.
 __device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
@@ -428,7 +431,7 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
         }
 #pragma unroll
         for (int x = 0; x < 2; x++) {
-            uint32_t h[4], l[4];
+            uint32_t h[4], l[4], hr[4], lr[4];
 #pragma unroll
             for (int j = 0; j < SPC; j++) {
                 const float X = x == 0 ? L.x[j].x : L.x[j].y;
@@ -436,7 +439,7 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
                     split_tf32(X * a[j].x, h[2 * j], l[2 * j]);
                     split_tf32(X * a[j].y, h[2 * j + 1], l[2 * j + 1]);
                 } else {
-                    split_bf16(X * a[j].x, X * a[j].y, h[j], l[j]);
+                    split_bf16_rot(X * a[j].x, X * a[j].y, h[j], l[j], hr[j], lr[j]);
                 }
             }
             st16(bh + o_re + 16 * x, h[0], h[1], h[2], h[3]);
@@ -445,8 +448,8 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
                 st16(bh + o_im + 16 * x, h[1] ^ 0x80000000u, h[0], h[3] ^ 0x80000000u, h[2]);
                 st16(blo + o_im + 16 * x, l[1] ^ 0x80000000u, l[0], l[3] ^ 0x80000000u, l[2]);
             } else {
-                st16(bh + o_im + 16 * x, rot_bf16(h[0]), rot_bf16(h[1]), rot_bf16(h[2]), rot_bf16(h[3]));
-                st16(blo + o_im + 16 * x, rot_bf16(l[0]), rot_bf16(l[1]), rot_bf16(l[2]), rot_bf16(l[3]));
+                st16(bh + o_im + 16 * x, hr[0], hr[1], hr[2], hr[3]);
+                st16(blo + o_im + 16 * x, lr[0], lr[1], lr[2], lr[3]);
             }
         }
     };
