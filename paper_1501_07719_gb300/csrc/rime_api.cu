@@ -65,13 +65,18 @@ void free_all(rime_ctx *c) {
                     c->d_gauss, c->d_alpha, c->d_src_extra, c->d_tau, c->d_rho, c->d_units,
                     c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
                     c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
-                    c->d_spart, c->d_scounter, c->d_sscale, c->d_sbuf[0], c->d_sbuf[1], c->d_schi,
+                    c->d_spart, c->d_scounter, c->d_sscale, c->d_schi,
                     c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    cudaEvent_t evs[] = {c->ev_start, c->ev_entry, c->ev_copied[0], c->ev_copied[1], c->ev_free[0], c->ev_free[1]};
-    for (cudaEvent_t e : evs)
+    for (void *p : c->d_sbuf)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : {c->ev_start, c->ev_entry, c->ev_upload})
         if (e) cudaEventDestroy(e);
+    for (int b = 0; b < rime_ctx::kStreamBufs; b++) {
+        if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
+        if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
+    }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->h_status) cudaFreeHost(c->h_status);
 }
@@ -98,6 +103,20 @@ cudaError_t reset_class(rime_ctx *c, int cls) {
 }  // namespace
 
 cudaError_t rime::reset_status_class(rime_ctx *c, int cls) { return reset_class(c, cls); }
+
+// Marks the end of the context's latest host-to-device upload on its stream:
+// the streamed chi^2 starts its chunk copies after it, so that they neither
+// queue ahead of an upload that the chunk kernels need nor wait for the
+// kernels queued after it.
+cudaError_t rime::mark_upload(rime_ctx *c) {
+    if (!c->ev_upload) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->ev_upload, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(c->ev_upload, c->stream);
+    if (e == cudaSuccess) c->upload_marked = true;
+    return e;
+}
 
 namespace {
 
@@ -170,6 +189,7 @@ rime_status upload_data(rime_ctx *c, const void *data, const void *weight) {
            "copying weights");
     }
     c->has_weight = weight != nullptr;
+    CK(c, mark_upload(c), "event");
     CK(c, reset_class(c, EC_DATA), "reset status");
     CK(c, launch_validate_data(c), "validating data");
     return RIME_OK;
@@ -186,6 +206,7 @@ rime_status upload_uvw(rime_ctx *c, const double *uvw, const double *pointing) {
            "copying pointing");
     }
     c->has_pointing = pointing != nullptr;
+    CK(c, mark_upload(c), "event");
     CK(c, reset_class(c, EC_UVW), "reset status");
     CK(c, launch_validate_uvw(c), "validating uvw");
     CK(c, launch_prep_delays(c), "delays");
@@ -320,6 +341,7 @@ rime_status rime_set_gains(rime_ctx *c, const double *gains) {
     if (!c->d_gains) CK(c, alloc(&c->d_gains, n * c->tsize()), "allocating gains");
     CK(c, cudaMemcpyAsync(c->d_gains_in, gains, n * sizeof(double), cudaMemcpyDefault, c->stream),
        "copying gains");
+    CK(c, mark_upload(c), "event");
     CK(c, reset_class(c, EC_GAINS), "reset status");
     CK(c, launch_convert_gains(c), "converting gains");
     c->has_gains = true;
@@ -353,7 +375,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
         size_t ts = c->tsize();
         size_t ndc = (size_t)c->dims.ntime * cap * c->dims.na;
         Alloc alloc{c};
-        CK(c, alloc((void **)&c->d_src_in, (2 + 4 * rows + 1 + 3 + 1) * cap * sizeof(double)), "allocating sources");
+        CK(c, alloc((void **)&c->d_src_in, rime_ctx::src_in_doubles(rows, cap) * sizeof(double)), "allocating sources");
         CK(c, alloc(&c->d_stokes, rows * cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_gauss, cap * 4 * ts), "allocating sources");
         CK(c, alloc(&c->d_alpha, cap * ts), "allocating sources");
@@ -381,6 +403,7 @@ rime_status rime_set_sources(rime_ctx *c, const rime_sources *src) {
             CK(c, cudaMemcpyAsync(c->src_kind(), src->kind, n * sizeof(int32_t), cudaMemcpyDefault, c->stream),
                "copying kind");
     }
+    if (n > 0) CK(c, mark_upload(c), "event");
     CK(c, reset_class(c, EC_SRC), "reset status");
     CK(c, reset_class(c, EC_MODE), "reset status");
     c->sources_set = true;

@@ -25,6 +25,7 @@
 namespace rime {
 
 constexpr double kCLight = 299792458.0;
+constexpr double kInvCLight = 1.0 / kCLight;
 constexpr double kPi = 3.141592653589793;
 constexpr double kLn2 = 0.6931471805599453;
 // pi^2 / (4 ln 2): the FWHM Gaussian's Fourier-transform constant
@@ -176,12 +177,16 @@ struct rime_ctx {
     bool sources_set = false;
     size_t src_cap = 0;               // sources the buffers below can hold
     size_t src_stokes_rows = 0;       // 1 or ntime
-    double *d_src_in = nullptr;       // copy of the FP64 parameters: lm, stokes, alpha, shape, kind
+    // copy of the FP64 parameters (lm, stokes, alpha, shape, kind), then the
+    // per-source geometry the delays need (l, m, n - 1, |lm|)
+    double *d_src_in = nullptr;
+    static size_t src_in_doubles(size_t rows, size_t cap) { return (2 + 4 * rows + 1 + 3 + 1 + 4) * cap; }
     double *src_lm() const { return d_src_in; }
     double *src_stokes() const { return d_src_in + 2 * src_cap; }
     double *src_alpha() const { return d_src_in + 2 * src_cap + 4 * src_cap * src_stokes_rows; }
     double *src_shape() const { return src_alpha() + src_cap; }
     int32_t *src_kind() const { return reinterpret_cast<int32_t *>(src_shape() + 3 * src_cap); }
+    double *src_geo() const { return src_shape() + 4 * src_cap; }
     bool has_kind = false;            // a kind array was given (disks may be present)
     bool has_shape = false;
     void *d_stokes = nullptr, *d_gauss = nullptr, *d_alpha = nullptr;
@@ -231,13 +236,18 @@ struct rime_ctx {
     size_t pair_cap = 0;                     // sources it holds
     int32_t *d_pair_kind = nullptr;
     double *d_chain_part = nullptr;          // [chains][ntime][blocks]: proposal chi^2 partials
-    // streamed chi^2 (rime_stream.cu): a copy stream, two chunk buffers
+    // streamed chi^2 (rime_stream.cu): a copy stream, a ring of chunk buffers
+    static constexpr int kStreamBufs = 4;
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_start = nullptr, ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_copied[kStreamBufs] = {}, ev_free[kStreamBufs] = {};
     bool stream_used = false;                // ev_start marks the previous streamed call's end
     cudaEvent_t ev_entry = nullptr;          // the context's stream at a call with device inputs
-    void *d_sbuf[2] = {nullptr, nullptr};   // chunk data, then chunk weights
+    cudaEvent_t ev_upload = nullptr;         // the context's stream after its latest upload copy
+    bool upload_marked = false;
+    void *d_sbuf[kStreamBufs] = {};          // chunk data, then chunk weights
     size_t sbuf_cap = 0;                     // bytes of each buffer
+    int sbuf_n = 0;                          // buffers allocated
+    int sbuf_asked = 0;                      // buffers asked for when they were (memory may allow fewer)
     double *d_schi = nullptr;                // chi^2 of each chunk
     size_t schi_cap = 0;
     int2 *d_stiles = nullptr;         // its tiles (p0, q0)
@@ -298,6 +308,7 @@ cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool c
 cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result);
 // rime_api.cu: clears one error class of the status block (stream-ordered)
 cudaError_t reset_status_class(rime_ctx *c, int cls);
+cudaError_t mark_upload(rime_ctx *c);
 // sets the message rime_last_error(NULL) returns (rime_api.cu)
 void set_global_error(const char *msg);
 // error reporting and the allocation cap shared by the entry points (rime_api.cu)

@@ -131,7 +131,7 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     size_t o_chan = L.take((size_t)dims->nchan * sizeof(ChanF) * 2);
     size_t o_uvwf = L.take(dims->precision == RIME_FP32 ? nta * sizeof(float4) : 0);
     size_t o_gains = L.take(gains ? nta * dims->nchan * 8 * ts : 0);
-    size_t o_srcin = L.take((2 + 4 * rows + 1 + 3 + 1) * cap * sizeof(double));
+    size_t o_srcin = L.take(rime_ctx::src_in_doubles(rows, cap) * sizeof(double));
     size_t o_stokes = L.take(rows * cap * 4 * ts);
     size_t o_gauss = L.take(cap * 4 * ts);
     size_t o_alpha = L.take(cap * ts);

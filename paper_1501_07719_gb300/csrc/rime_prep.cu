@@ -96,7 +96,7 @@ __global__ void k_convert_gains(long long n, const double *in, T *out, DevStatus
 template <typename T>
 __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, const double *stokes,
                                const double *alpha, const double *shape, const int32_t *kind, T *o_stokes,
-                               T *o_gauss, T *o_alpha, T *o_extra, DevStatus *st) {
+                               T *o_gauss, T *o_alpha, T *o_extra, double *o_geo, DevStatus *st) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long nst = (long long)stokes_rows * nsrc;
     if (i < nst) {
@@ -111,6 +111,15 @@ __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, cons
     }
     if (i >= nsrc) return;
     double l = lm[2 * i], m = lm[2 * i + 1], a = alpha[i];
+    {
+        // eq. 3's direction cosines: n - 1 = -(l^2+m^2)/(1+n) (no
+        // cancellation); |lm| is the beam radius without pointing errors
+        const double r2 = l * l + m * m;
+        o_geo[4 * i + 0] = l;
+        o_geo[4 * i + 1] = m;
+        o_geo[4 * i + 2] = -r2 / (1.0 + sqrt(1.0 - r2));
+        o_geo[4 * i + 3] = hypot(l, m);
+    }
     double maj = 0.0, mn = 0.0, pa = 0.0;
     if (shape) {
         maj = shape[3 * i];
@@ -155,38 +164,44 @@ __global__ void k_prep_sources(int nsrc, int stokes_rows, const double *lm, cons
 }
 
 // Per (t, s, a): geometric delay tau = (u l + v m + w (n - 1)) / c in
-// seconds (eq. 3 without the frequency), with n - 1 = -(l^2+m^2)/(1+n) (no
-// cancellation), and the beam radius rho = |(l, m) - dl_ta| of eq. 4.
-template <bool FP64>
-__global__ void k_prep_delays(int ntime, int nsrc, int na, const double *uvw, const double *pointing,
-                              const double *lm, void *tau_out, void *rho_out) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long n = (long long)ntime * nsrc * na;
-    if (i >= n) return;
-    int a = (int)(i % na);
-    long long ts = i / na;
-    int s = (int)(ts % nsrc);
-    int t = (int)(ts / nsrc);
-    double l = lm[2 * s], m = lm[2 * s + 1];
-    double r2 = l * l + m * m;
-    double n1 = -r2 / (1.0 + sqrt(1.0 - r2));
-    const double *x = uvw + 3 * ((long long)t * na + a);
-    double tau = (x[0] * l + x[1] * m + x[2] * n1) / kCLight;
-    double dl = 0.0, dm = 0.0;
+// seconds (eq. 3 without the frequency) and the beam radius rho = |(l, m) -
+// dl_ta| of eq. 4, from the per-source geometry (l, m, n - 1, |lm|) that the
+// source kernel writes. A few FP64 operations per entry: the square root and
+// division per source are done once there, 1/c is a constant, and the index
+// arithmetic is 32-bit unless the table has 2^31 entries or more.
+template <bool FP64, typename I>
+__device__ __forceinline__ void prep_delay(I i, int nsrc, int na, const double *uvw, const double *pointing,
+                                           const double *geo, void *tau_out, void *rho_out) {
+    const int a = (int)(i % (I)na);
+    const I ts = i / (I)na;
+    const int s = (int)(ts % (I)nsrc);
+    const I t = ts / (I)nsrc;
+    const double *g = geo + 4 * s;   // 8-byte aligned only
+    const long long ta = (long long)t * na + a;
+    const double *x = uvw + 3 * ta;
+    const double tau = fma(x[0], g[0], fma(x[1], g[1], x[2] * g[2])) * kInvCLight;
+    double rho = g[3];
     if (pointing) {
-        dl = pointing[2 * ((long long)t * na + a)];
-        dm = pointing[2 * ((long long)t * na + a) + 1];
+        const double dl = g[0] - pointing[2 * ta], dm = g[1] - pointing[2 * ta + 1];
+        rho = sqrt(fma(dl, dl, dm * dm));
     }
-    double rho = hypot(l - dl, m - dm);
     if (FP64) {
         reinterpret_cast<double *>(tau_out)[i] = tau;
         reinterpret_cast<double *>(rho_out)[i] = rho;
     } else {
-        float hi = (float)tau;
-        float lo = (float)(tau - (double)hi);
+        const float hi = (float)tau;
+        const float lo = (float)(tau - (double)hi);
         reinterpret_cast<float2 *>(tau_out)[i] = make_float2(hi, lo);
         reinterpret_cast<float *>(rho_out)[i] = (float)rho;
     }
+}
+template <bool FP64>
+__global__ void k_prep_delays(long long n, int nsrc, int na, const double *uvw, const double *pointing,
+                              const double *geo, void *tau_out, void *rho_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (n <= 0x7fffffffLL) prep_delay<FP64>((int)i, nsrc, na, uvw, pointing, geo, tau_out, rho_out);
+    else prep_delay<FP64>(i, nsrc, na, uvw, pointing, geo, tau_out, rho_out);
 }
 
 // sum ln(2 pi / w) over all visibilities (single block, fixed order).
@@ -267,11 +282,11 @@ cudaError_t launch_prep_sources(rime_ctx *c) {
     if (c->dims.precision == RIME_FP64)
         k_prep_sources<double><<<blocks_for(n), kThreads, 0, c->stream>>>(
             nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, kind, (double *)c->d_stokes,
-            (double *)c->d_gauss, (double *)c->d_alpha, (double *)c->d_src_extra, c->d_status);
+            (double *)c->d_gauss, (double *)c->d_alpha, (double *)c->d_src_extra, c->src_geo(), c->d_status);
     else
         k_prep_sources<float><<<blocks_for(n), kThreads, 0, c->stream>>>(
             nsrc, rows, c->src_lm(), c->src_stokes(), c->src_alpha(), shape, kind, (float *)c->d_stokes,
-            (float *)c->d_gauss, (float *)c->d_alpha, (float *)c->d_src_extra, c->d_status);
+            (float *)c->d_gauss, (float *)c->d_alpha, (float *)c->d_src_extra, c->src_geo(), c->d_status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_prep_delays(c);
@@ -283,11 +298,11 @@ cudaError_t launch_prep_delays(rime_ctx *c) {
     long long nd = (long long)c->dims.ntime * nsrc * c->dims.na;
     const double *pt = c->has_pointing ? c->d_pointing : nullptr;
     if (c->dims.precision == RIME_FP64)
-        k_prep_delays<true><<<blocks_for(nd), kThreads, 0, c->stream>>>(
-            c->dims.ntime, nsrc, c->dims.na, c->d_uvw, pt, c->src_lm(), c->d_tau, c->d_rho);
+        k_prep_delays<true><<<blocks_for(nd), kThreads, 0, c->stream>>>(nd, nsrc, c->dims.na, c->d_uvw, pt,
+                                                                         c->src_geo(), c->d_tau, c->d_rho);
     else
-        k_prep_delays<false><<<blocks_for(nd), kThreads, 0, c->stream>>>(
-            c->dims.ntime, nsrc, c->dims.na, c->d_uvw, pt, c->src_lm(), c->d_tau, c->d_rho);
+        k_prep_delays<false><<<blocks_for(nd), kThreads, 0, c->stream>>>(nd, nsrc, c->dims.na, c->d_uvw, pt,
+                                                                          c->src_geo(), c->d_tau, c->d_rho);
     return cudaGetLastError();
 }
 

@@ -4,12 +4,19 @@
 // The paper subdivides a problem that does not fit the GPU along time and
 // keeps two solvers, so that the transfer of one chunk's data overlaps the
 // computation of the other's; the chunk chi^2 values are then added. Here the
-// two "solvers" are two device buffers: chunk i's data and weights are copied
-// on a second stream into buffer i mod 2 while the fused kernel reduces chunk
-// i - 1 on the context's stream. Events order the two streams:
+// "solvers" are a ring of up to four device buffers: chunk i's data and
+// weights are copied on a second stream into buffer i mod n while the fused
+// kernel reduces earlier chunks on the context's stream. More than two
+// buffers let the copies run ahead while the context's stream is still busy
+// with work queued before the call (the uploads of uvw, gains and sources of
+// the same step), so the transfers keep the host link busy from the start.
+// Events order the two streams:
 //   copied[b]  (copy stream)    -> the kernel of the chunk in buffer b may start;
-//   free[b]    (context stream) -> buffer b may be overwritten (two chunks on);
-//   start      (context stream, end of the previous call) -> the buffers are free.
+//   free[b]    (context stream) -> buffer b may be overwritten (n chunks on);
+//   start      (context stream, end of the previous call) -> the buffers are free;
+//   upload     (context stream, after its latest upload copy) -> the chunk
+//              copies may start: they overlap the kernels that follow the
+//              uploads (input checks, delays) but do not queue ahead of them.
 // Each chunk's data are checked on arrival; each chunk's kernel writes its
 // chi^2 to its own slot, and one thread adds the slots in chunk order, so the
 // result does not depend on the chunking schedule's timing.
@@ -28,37 +35,51 @@ __global__ void k_sum_in_order(int n, const double *in, double *out, const DevSt
     *out = s;
 }
 
-// Grows the two chunk buffers to `bytes` each and the per-chunk results to
-// `nchunks`; creates the copy stream and events on first use.
-cudaError_t ensure(rime_ctx *c, size_t bytes, int nchunks) {
+// Makes `nbuf` chunk buffers of `bytes` each (fewer, but at least two, when
+// the ring would take more than half of the free device memory) and room for
+// `nchunks` chunk results; creates the copy stream and events on first use.
+// Returns the number of buffers to use in `*nuse`.
+cudaError_t ensure(rime_ctx *c, size_t bytes, int nbuf, int nchunks, int *nuse) {
     cudaError_t e;
     if (!c->copy_stream) {
         e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
-        cudaEvent_t *evs[] = {&c->ev_start, &c->ev_entry, &c->ev_copied[0], &c->ev_copied[1], &c->ev_free[0],
-                              &c->ev_free[1]};
-        for (cudaEvent_t *ev : evs) {
-            e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+        e = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        e = cudaEventCreateWithFlags(&c->ev_entry, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        for (int b = 0; b < rime_ctx::kStreamBufs; b++) {
+            e = cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            e = cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming);
             if (e != cudaSuccess) return e;
         }
     }
-    Alloc alloc{c};
-    if (bytes > c->sbuf_cap) {
-        for (int b = 0; b < 2; b++) {
+    if (bytes > c->sbuf_cap || nbuf > c->sbuf_asked) {
+        for (int b = 0; b < rime_ctx::kStreamBufs; b++) {
             if (c->d_sbuf[b]) cudaFree(c->d_sbuf[b]);
             c->d_sbuf[b] = nullptr;
         }
         c->sbuf_cap = 0;
-        for (int b = 0; b < 2; b++) {
+        c->sbuf_n = 0;
+        c->sbuf_asked = nbuf;
+        size_t free_b = 0, total_b = 0;
+        if (nbuf > 2 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            nbuf = (int)std::max<size_t>(2, std::min<size_t>(nbuf, free_b / 2 / std::max<size_t>(bytes, 1)));
+        Alloc alloc{c};
+        for (int b = 0; b < nbuf; b++) {
             e = alloc(&c->d_sbuf[b], bytes);
             if (e != cudaSuccess) return e;
+            c->sbuf_n = b + 1;
         }
         c->sbuf_cap = bytes;
     }
+    *nuse = std::min(nbuf, c->sbuf_n);
     if ((size_t)nchunks > c->schi_cap) {
         if (c->d_schi) cudaFree(c->d_schi);
         c->d_schi = nullptr;
         c->schi_cap = 0;
+        Alloc alloc{c};
         e = alloc((void **)&c->d_schi, (size_t)nchunks * sizeof(double));
         if (e != cudaSuccess) return e;
         c->schi_cap = nchunks;
@@ -106,12 +127,18 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     const size_t ts = c->tsize();
     const size_t vis_t = (size_t)c->nbl * c->dims.nchan;           // visibilities per timestep
     const size_t dbytes = vis_t * 8 * ts, wbytes = vis_t * ts;      // per timestep
-    CKS(c, ensure(c, (size_t)nt * std::max(dbytes + wbytes, (size_t)16), nchunks), "allocating chunk buffers");
+    int nbuf = 0;
+    CKS(c, ensure(c, (size_t)nt * std::max(dbytes + wbytes, (size_t)16), std::min(nchunks, rime_ctx::kStreamBufs),
+                  nchunks, &nbuf),
+        "allocating chunk buffers");
     CKS(c, reset_status_class(c, EC_SDATA), "reset status");
     // the copy stream must not overwrite a buffer that the previous streamed
     // call's kernels still read; it need not wait for the rest of the
     // context's work (uploads of uvw, gains, sources), which the copies overlap
     if (c->stream_used) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0), "stream wait");
+    // nor queue ahead of the context's own uploads (one DMA queue serves
+    // both streams' host-to-device copies in the order they become ready)
+    if (c->upload_marked) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_upload, 0), "stream wait");
     // device-memory inputs may be written by work queued on the context's
     // stream: then the copies follow that work
     auto on_device = [](const void *p) {
@@ -129,12 +156,12 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     const char *hd = static_cast<const char *>(data);
     const char *hw = static_cast<const char *>(weight);
     for (int i = 0; i < nchunks; i++) {
-        const int b = i & 1;
+        const int b = i % nbuf;
         const int t0 = i == 0 ? 0 : first + (i - 1) * nt;
         const int nti = std::min(i == 0 ? first : nt, ntime - t0);
         char *bd = static_cast<char *>(c->d_sbuf[b]);
         char *bw = bd + (size_t)nt * dbytes;
-        if (i >= 2) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0), "stream wait");
+        if (i >= nbuf) CKS(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0), "stream wait");
         CKS(c, cudaMemcpyAsync(bd, hd + (size_t)t0 * dbytes, (size_t)nti * dbytes, cudaMemcpyDefault, c->copy_stream),
             "copying a data chunk");
         if (hw)

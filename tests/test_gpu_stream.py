@@ -53,6 +53,32 @@ def test_streamed_equals_resident_and_oracle(na, kernel, precision):
     r.close()
 
 
+@pytest.mark.parametrize("kernel", [None, "tiled"])
+def test_streamed_follows_uploads_queued_before_it(kernel):
+    """The chunk copies run ahead of the context's stream (a ring of up to
+    four buffers); the chunk kernels still see the gains and sources set just
+    before the call, over more chunks than buffers."""
+    import copy
+    import torch
+    import paper_1501_07719_gb300 as R
+    inp = _streamed_case(13, "f32")
+    r = gpu_ctx(inp, "f32")
+    if kernel == "tiled":
+        r.set_kernel(R.RIME_KERNEL_TILED)
+    w = np.asarray(inp["weight"], dtype=np.float32)
+    pinned_d = torch.from_numpy(np.ascontiguousarray(inp["data"])).pin_memory()
+    pinned_w = torch.from_numpy(w).pin_memory()
+    for step in range(3):
+        src = copy.deepcopy(inp["sources"])
+        src["stokes"] = src["stokes"] * (1.0 + 0.25 * step)
+        r.set_gains(inp["gains"] * (1.0 - 0.1 * step))
+        r.set_sources(src)
+        got = r.chi2_streamed(pinned_d, pinned_w, 1)
+        expect = r.chi2()
+        assert rel_err(got, expect) <= 1e-13, (step, got, expect)
+    r.close()
+
+
 def test_streamed_unit_weights_and_context_without_data():
     import paper_1501_07719_gb300 as R
     inp = _streamed_case(9, "f64")
