@@ -207,10 +207,14 @@ rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 /* chi^2 (eq. 7, without the ln-weight term) of an observation whose data
  * and weights stay in host memory, streamed to the GPU in chunks of
  * chunk_ntime timesteps (the time subdivision of Sec. 4.4): while the fused
- * kernel reduces one chunk, the next is copied on a second stream into the
- * other of two device buffers, and the chunk values are added in chunk order.
- * Device memory for the data is two chunks, not the observation: an
- * observation larger than the GPU fits. The context's uvw, gains and sources
+ * kernel reduces earlier chunks (alternating between the context's stream
+ * and a second kernel stream), the next ones are copied on a copy stream
+ * into a ring of up to eight device buffers, and the chunk values are added
+ * in chunk order. The copies start after the context's latest upload
+ * (rime_set_uvw / _gains / _sources / _data) has been copied. Device memory
+ * for the data is the ring (at most half of the free memory, at least two
+ * chunks), not the observation: an observation larger than the GPU fits.
+ * The context's uvw, gains and sources
  * cover the whole observation; its own data buffer is not used (the context
  * may be created with data = NULL). The tensor-core modes do not apply.
  *   data         [ntime][nbl][nchan][4] complex, host memory (pinned memory
@@ -227,8 +231,8 @@ rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 rime_status rime_chi2_streamed(rime_ctx *ctx, const void *data, const void *weight, int32_t chunk_ntime,
                                double *chi2);
 
-/* The chunk length rime_chi2_streamed picks: about four waves of the fused
- * kernel per chunk, at most ntime. 0 for a NULL context. */
+/* The chunk length rime_chi2_streamed picks: about one wave of the fused
+ * kernel per chunk (2 blocks per SM), at most ntime. 0 for a NULL context. */
 int32_t rime_stream_chunk_ntime(const rime_ctx *ctx);
 
 /* Chains: per-chain residuals for a sampler whose proposals move a few

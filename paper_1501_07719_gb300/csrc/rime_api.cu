@@ -71,13 +71,15 @@ void free_all(rime_ctx *c) {
         if (p) cudaFree(p);
     for (void *p : c->d_sbuf)
         if (p) cudaFree(p);
-    for (cudaEvent_t e : {c->ev_start, c->ev_entry, c->ev_upload})
+    if (c->d_stream_counters) cudaFree(c->d_stream_counters);
+    for (cudaEvent_t e : {c->ev_start, c->ev_entry, c->ev_upload, c->ev_k2})
         if (e) cudaEventDestroy(e);
     for (int b = 0; b < rime_ctx::kStreamBufs; b++) {
         if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
         if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->kstream2) cudaStreamDestroy(c->kstream2);
     if (c->h_status) cudaFreeHost(c->h_status);
 }
 

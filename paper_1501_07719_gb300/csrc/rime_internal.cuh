@@ -237,12 +237,15 @@ struct rime_ctx {
     int32_t *d_pair_kind = nullptr;
     double *d_chain_part = nullptr;          // [chains][ntime][blocks]: proposal chi^2 partials
     // streamed chi^2 (rime_stream.cu): a copy stream, a ring of chunk buffers
-    static constexpr int kStreamBufs = 4;
+    static constexpr int kStreamBufs = 8;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_copied[kStreamBufs] = {}, ev_free[kStreamBufs] = {};
     bool stream_used = false;                // ev_start marks the previous streamed call's end
     cudaEvent_t ev_entry = nullptr;          // the context's stream at a call with device inputs
     cudaEvent_t ev_upload = nullptr;         // the context's stream after its latest upload copy
+    cudaStream_t kstream2 = nullptr;         // odd chunks' kernels (even ones: the context's stream)
+    cudaEvent_t ev_k2 = nullptr;             // kstream2's last chunk kernel
+    unsigned *d_stream_counters = nullptr;   // last-block counters of the two kernel streams
     bool upload_marked = false;
     void *d_sbuf[kStreamBufs] = {};          // chunk data, then chunk weights
     size_t sbuf_cap = 0;                     // bytes of each buffer
@@ -273,7 +276,7 @@ cudaError_t launch_ln_norm(rime_ctx *c);
 // checks nvis visibilities' data / weights (either may be NULL) and flags class
 // cls with the index i0 + i of the first bad one
 cudaError_t launch_validate_chunk(rime_ctx *c, long long nvis, const void *data, const void *weight, int cls,
-                                  long long i0);
+                                  long long i0, cudaStream_t stream = nullptr);
 // rime_grad.cu
 cudaError_t launch_grad_src(rime_ctx *c, double *grad_src);
 // launchers (rime_fused.cu)
@@ -302,6 +305,8 @@ cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, 
 // the same with prepared parameters over timesteps [P.t_begin, P.t_begin + nt)
 cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt,
                                  cudaStream_t stream = nullptr);
+// blocks of one timestep of the small-array kernel (launches cover whole timesteps)
+long long narrow_blocks_per_time(rime_ctx *c);
 // predict (chi2 = false) or chi^2 over all sources with the kernel that suits the array
 cudaError_t launch_fused_auto(rime_ctx *c, void *vis_out, double *result, bool chi2);
 // rime_split.cu

@@ -384,6 +384,12 @@ cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, 
     return launch_narrow_params(c, mode, P, c->dims.ntime);
 }
 
+long long narrow_blocks_per_time(rime_ctx *c) {
+    if (c->nsm <= 0 && cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->nsm = 152;
+    return narrow::shape_for(c->dims.na, c->dims.ntime, c->dims.nchan, c->nsm).ngroups;
+}
+
 cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt, cudaStream_t stream) {
     if (!stream) stream = c->stream;
     using namespace narrow;

@@ -250,13 +250,14 @@ cudaError_t launch_validate_data(rime_ctx *c) {
 }
 
 cudaError_t launch_validate_chunk(rime_ctx *c, long long nvis, const void *data, const void *weight, int cls,
-                                  long long i0) {
+                                  long long i0, cudaStream_t stream) {
     if (nvis == 0) return cudaSuccess;
+    if (!stream) stream = c->stream;
     if (c->dims.precision == RIME_FP64)
-        k_validate_data<double><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
+        k_validate_data<double><<<blocks_for(nvis), kThreads, 0, stream>>>(
             nvis, (const double *)data, (const double *)weight, c->d_status, cls, i0);
     else
-        k_validate_data<float><<<blocks_for(nvis), kThreads, 0, c->stream>>>(
+        k_validate_data<float><<<blocks_for(nvis), kThreads, 0, stream>>>(
             nvis, (const float *)data, (const float *)weight, c->d_status, cls, i0);
     return cudaGetLastError();
 }
