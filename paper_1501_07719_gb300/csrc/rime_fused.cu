@@ -551,12 +551,39 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                                                           f2(ly4.x, ly4.y));
                         const float2 g1 = shape2<GENERAL>(disk, qp, up, vp, f2(q4.z, q4.w), f2(lx4.z, lx4.w),
                                                           f2(ly4.z, ly4.w));
-                        accumulate2g(acc[2 * h], ax, ay, bx[2 * h], by[2 * h], g0, s01, s23);
-                        accumulate2g(acc[2 * h + 1], ax, ay, bx[2 * h + 1], by[2 * h + 1], g1, s01, s23);
+                        const float2 nax = f2(-ax.x, -ax.y);
+                        const float2 zr0 = __fmul2_rn(__ffma2_rn(ax, bx[2 * h], __fmul2_rn(ay, by[2 * h])), g0);
+                        const float2 zi0 = __fmul2_rn(__ffma2_rn(ay, bx[2 * h], __fmul2_rn(nax, by[2 * h])), g0);
+                        const float2 zr1 = __fmul2_rn(__ffma2_rn(ax, bx[2 * h + 1], __fmul2_rn(ay, by[2 * h + 1])), g1);
+                        const float2 zi1 = __fmul2_rn(__ffma2_rn(ay, bx[2 * h + 1], __fmul2_rn(nax, by[2 * h + 1])), g1);
+                        const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
+#pragma unroll
+                        for (int c = 0; c < 4; c++) {
+                            acc[2 * h].re[c] = __ffma2_rn(zr0, X[c], acc[2 * h].re[c]);
+                            acc[2 * h + 1].re[c] = __ffma2_rn(zr1, X[c], acc[2 * h + 1].re[c]);
+                            acc[2 * h].im[c] = __ffma2_rn(zi0, X[c], acc[2 * h].im[c]);
+                            acc[2 * h + 1].im[c] = __ffma2_rn(zi1, X[c], acc[2 * h + 1].im[c]);
+                        }
                     }
                 } else {
 #pragma unroll
-                    for (int h = 0; h < 4; h++) accumulate2(acc[h], ax, ay, bx[h], by[h], s01, s23);
+                    {
+                        float2 zr[4], zi[4];
+                        const float2 nax = f2(-ax.x, -ax.y);
+#pragma unroll
+                        for (int h = 0; h < 4; h++) {
+                            zr[h] = __ffma2_rn(ax, bx[h], __fmul2_rn(ay, by[h]));
+                            zi[h] = __ffma2_rn(ay, bx[h], __fmul2_rn(nax, by[h]));
+                        }
+                        const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
+#pragma unroll
+                        for (int c = 0; c < 4; c++)
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                acc[h].re[c] = __ffma2_rn(zr[h], X[c], acc[h].re[c]);
+                                acc[h].im[c] = __ffma2_rn(zi[h], X[c], acc[h].im[c]);
+                            }
+                    }
                 }
             }
         } else if (role == 2) {
