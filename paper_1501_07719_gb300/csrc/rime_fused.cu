@@ -301,14 +301,22 @@ constexpr int NSLOT = 8;             // baselines per thread
 __device__ __forceinline__ int apad(int a) { return a + ((a >> 3) << 2); }
 
 // The source sum runs on packed pairs of FP32 values (two FMAs per
-// instruction) over pairs of adjacent baseline slots: the per-antenna
-// factors are staged as separate real and imaginary rows, so the column
-// factors of slots j and j+1 are one 8-byte pair.
+// instruction) over pairs of adjacent baseline slots: the per-antenna factors
+// are staged as separate real and imaginary rows, so the column factors of
+// slots j and j+1 are one 8-byte pair.
+//
+// Body tiles are 2 x 4: rows p, p + 1 (p even) against columns q .. q + 3
+// (q a multiple of 4) of another 8-antenna block, so that per source a thread
+// loads its two row factors (two 8-byte loads), its four column factors (two
+// 16-byte loads) and the source's scaled Stokes vector (one 16-byte broadcast
+// load) for 48 packed FMAs; shared-memory bandwidth, not the FMA pipe, bounds
+// tiles that load more per FMA (a 1 x 8 tile needs eight loads).
 //
 // The Gaussian exponent of baseline (p, q) for source s is the quadratic form
 // Qf(x_p - x_q) of the antenna coordinates x = (u, v); it is evaluated as
 // Qf(x_p) + Qf(x_q) - x_p . L(x_q) with L(x) = grad Qf(x), from per-antenna
-// values staged with the factors.
+// values staged with the factors. A chunk of point sources runs a loop
+// without shape factors.
 struct Smem {
     float Kx[SC * RSTR], Ky[SC * RSTR];            // staged A = x + iy, row antennas
     float Cx[SC * CSTR], Cy[SC * CSTR];            // column antennas (off-diagonal units)
@@ -319,8 +327,8 @@ struct Smem {
     float4 rSt[SC];             // prefetched Stokes
     float4 rG[SC];              // prefetched Gaussian coefficients
     float rAl[SC];              // prefetched spectral indices
-    float4 St[SC][2];           // (I, I, Q, Q), (U, U, V, V), scaled (see staging)
-    float Gf[SC];               // 1 for a Gaussian source
+    float4 St[SC];              // (I, Q, U, V) scaled (see staging)
+    float Gf[SC];               // source kind: 0 point, 1 Gaussian, 2 exponential disk
     float2 uv[NLOC];            // antenna (u, v) at this timestep, unit order
     float GG[NLOC * 8];         // gradient mode: per-antenna gains gradient of this block
     double red[32];
@@ -328,9 +336,10 @@ struct Smem {
 
 // Local (row, column) antennas of slot j of a thread tile; rev = 1 when the
 // tile forms the pair in the order (column, row) and the accumulated sums
-// must be conjugated. Body tile: row p, columns q .. q+7. Head tile: with
-// x_i = b0 + ((fold + i) mod 8), slots 0..3 pair x_0 with x_1..x_4 and slots
-// 4..6 pair x_4 with x_5..x_7; slot 7 is unused.
+// must be conjugated. Body tile: rows p, p + 1 against columns q .. q + 3,
+// slot j = 4 r + c. Head tile: with x_i = b0 + ((fold + i) mod 8), slots 0..3
+// pair x_0 with x_1..x_4 and slots 4..6 pair x_4 with x_5..x_7; slot 7 is
+// unused.
 __device__ __forceinline__ void slot_pair(const Tile &tl, int role, int j, int &p, int &q, bool &rev) {
     if (role == 2) {
         const int b0 = tl.p, r = tl.fold;
@@ -340,8 +349,8 @@ __device__ __forceinline__ void slot_pair(const Tile &tl, int role, int j, int &
         p = rev ? xb : xa;
         q = rev ? xa : xb;
     } else {
-        p = tl.p;
-        q = tl.q + j;
+        p = tl.p + (j >> 2);
+        q = tl.q + (j & 3);
         rev = false;
     }
 }
@@ -349,28 +358,21 @@ __device__ __forceinline__ void slot_pair(const Tile &tl, int role, int j, int &
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Two slots: z = a conj(b) for rows (ax, ay) (as pairs over the two slots)
-// and columns (bx, by), optionally times the Gaussian factors, accumulated
-// against (I, Q, U, V): acc[X][0] holds the real parts of the two slots,
-// acc[X][1] the imaginary parts.
+// and columns (bx, by), optionally times the shape factors, accumulated
+// against (I, Q, U, V): acc.re holds the real parts of the two slots' sums,
+// acc.im the imaginary parts.
 struct Pair {
     float2 re[4], im[4];
 };
-__device__ __forceinline__ void accumulate2(Pair &acc, float2 ax, float2 ay, float2 bx, float2 by,
-                                            const float4 &s01, const float4 &s23) {
-    const float2 zr = __ffma2_rn(ax, bx, __fmul2_rn(ay, by));
-    const float2 zi = __ffma2_rn(ay, bx, __fmul2_rn(f2(-ax.x, -ax.y), by));
-    const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        acc.re[c] = __ffma2_rn(zr, X[c], acc.re[c]);
-        acc.im[c] = __ffma2_rn(zi, X[c], acc.im[c]);
+template <bool SHAPE>
+__device__ __forceinline__ void accumulate2(Pair &acc, float2 ax, float2 ay, float2 bx, float2 by, float2 g,
+                                            const float2 (&X)[4]) {
+    float2 zr = __ffma2_rn(ax, bx, __fmul2_rn(ay, by));
+    float2 zi = __ffma2_rn(ay, bx, __fmul2_rn(f2(-ax.x, -ax.y), by));
+    if (SHAPE) {
+        zr = __fmul2_rn(zr, g);
+        zi = __fmul2_rn(zi, g);
     }
-}
-__device__ __forceinline__ void accumulate2g(Pair &acc, float2 ax, float2 ay, float2 bx, float2 by, float2 g,
-                                             const float4 &s01, const float4 &s23) {
-    const float2 zr = __fmul2_rn(__ffma2_rn(ax, bx, __fmul2_rn(ay, by)), g);
-    const float2 zi = __fmul2_rn(__ffma2_rn(ay, bx, __fmul2_rn(f2(-ax.x, -ax.y), by)), g);
-    const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
 #pragma unroll
     for (int c = 0; c < 4; c++) {
         acc.re[c] = __ffma2_rn(zr, X[c], acc.re[c]);
@@ -388,6 +390,79 @@ __device__ __forceinline__ float2 shape2(bool disk, float2 qp, float2 up, float2
         return f2(r0 * r0 * r0, r1 * r1 * r1);
     }
     return f2(ex2_approx(e.x), ex2_approx(e.y));
+}
+
+// One chunk of sources for a 2 x 4 body tile (rows at ip, columns at iq of
+// the staged rows; cstr the column rows' stride).
+template <bool SHAPE, bool GENERAL>
+__device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const float *KxC, const float *KyC,
+                                           const float *QC, const float *LxC, const float *LyC, int cstr, int ip,
+                                           int iq, int sc, float2 (&up)[2], float2 (&vp)[2]) {
+#pragma unroll 1
+    for (int s = 0; s < sc; s++) {
+        const float2 kr = *reinterpret_cast<const float2 *>(S.Kx + s * RSTR + ip);
+        const float2 ki = *reinterpret_cast<const float2 *>(S.Ky + s * RSTR + ip);
+        const float4 bx4 = *reinterpret_cast<const float4 *>(KxC + s * cstr + iq);
+        const float4 by4 = *reinterpret_cast<const float4 *>(KyC + s * cstr + iq);
+        const float4 x = S.St[s];
+        const float2 X[4] = {f2(x.x, x.x), f2(x.y, x.y), f2(x.z, x.z), f2(x.w, x.w)};
+        const float2 bx[2] = {f2(bx4.x, bx4.y), f2(bx4.z, bx4.w)}, by[2] = {f2(by4.x, by4.y), f2(by4.z, by4.w)};
+        float2 g[4] = {f2(1.f, 1.f), f2(1.f, 1.f), f2(1.f, 1.f), f2(1.f, 1.f)};
+        if (SHAPE) {
+            const bool disk = S.Gf[s] > 1.5f;
+            const float2 qr = *reinterpret_cast<const float2 *>(S.Qr + s * RSTR + ip);
+            const float4 q4 = *reinterpret_cast<const float4 *>(QC + s * cstr + iq);
+            const float4 lx4 = *reinterpret_cast<const float4 *>(LxC + s * cstr + iq);
+            const float4 ly4 = *reinterpret_cast<const float4 *>(LyC + s * cstr + iq);
+            const float2 qq[2] = {f2(q4.x, q4.y), f2(q4.z, q4.w)};
+            const float2 lx[2] = {f2(lx4.x, lx4.y), f2(lx4.z, lx4.w)}, ly[2] = {f2(ly4.x, ly4.y), f2(ly4.z, ly4.w)};
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int r = h >> 1, c = h & 1;
+                const float qpr = r ? qr.y : qr.x;
+                g[h] = shape2<GENERAL>(disk, f2(qpr, qpr), up[r], vp[r], qq[c], lx[c], ly[c]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const int r = h >> 1, c = h & 1;
+            const float xr = r ? kr.y : kr.x, yr = r ? ki.y : ki.x;
+            accumulate2<SHAPE>(acc[h], f2(xr, xr), f2(yr, yr), bx[c], by[c], g[h], X);
+        }
+    }
+}
+
+// One chunk for a head tile: pairs inside one 8-antenna block, rows x_0 and x_4.
+template <bool SHAPE, bool GENERAL>
+__device__ __forceinline__ void head_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const Tile &tl, int sc,
+                                           float2 (&up)[2], float2 (&vp)[2]) {
+    const int hb = apad(tl.p), r = tl.fold;
+    int ho[8];   // shared-memory offsets of x_0..x_7 (one 8-antenna block)
+#pragma unroll
+    for (int i = 0; i < 8; i++) ho[i] = hb + ((r + i) & 7);
+#pragma unroll 1
+    for (int s = 0; s < sc; s++) {
+        const float4 x = S.St[s];
+        const float2 X[4] = {f2(x.x, x.x), f2(x.y, x.y), f2(x.z, x.z), f2(x.w, x.w)};
+        const float *kx = S.Kx + s * RSTR, *ky = S.Ky + s * RSTR;
+        const float2 ax[2] = {f2(kx[ho[0]], kx[ho[0]]), f2(kx[ho[4]], kx[ho[4]])};
+        const float2 ay[2] = {f2(ky[ho[0]], ky[ho[0]]), f2(ky[ho[4]], ky[ho[4]])};
+        const bool disk = S.Gf[s] > 1.5f;
+        const float *qq = S.Qr + s * RSTR, *lx = S.Lxr + s * RSTR, *ly = S.Lyr + s * RSTR;
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const int r2 = h < 2 ? 0 : 1;
+            const int c0 = ho[2 * h + 1], c1 = h < 3 ? ho[2 * h + 2] : ho[0];   // slot 7 unused
+            const float2 bx = f2(kx[c0], kx[c1]), by = f2(ky[c0], ky[c1]);
+            float2 g = f2(1.f, 1.f);
+            if (SHAPE) {
+                const float qps = qq[ho[4 * r2]];
+                g = shape2<GENERAL>(disk, f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]), f2(lx[c0], lx[c1]),
+                                    f2(ly[c0], ly[c1]));
+            }
+            accumulate2<SHAPE>(acc[h], ax[r2], ay[r2], bx, by, g, X);
+        }
+    }
 }
 
 // One work item: timestep t, channel k, antenna unit u, sources [sb, se).
@@ -474,6 +549,8 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     for (int h = 0; h < NSLOT / 2; h++)
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
+    // the rows' antenna coordinates, as pairs (filled after the first barrier)
+    float2 up[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, vp[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 
     for (int s0 = sb; s0 < se; s0 += SC) {
         const int sc = min(SC, se - s0);
@@ -507,6 +584,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             s += it_ds;
             if (a >= nloc) { a -= nloc; s += 1; }
         }
+        bool ext = false;
         if (tid < sc) {
             // spectral factor (nu / nu_ref)^alpha = 2^(2 alpha hlr) of eq. 2
             float f = exp2f(2.0f * S.rAl[tid] * ch.hlr);
@@ -515,109 +593,31 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 f *= E * E;
             }
             float4 st = S.rSt[tid];
-            S.St[tid][0] = make_float4(st.x * f, st.x * f, st.y * f, st.y * f);
-            S.St[tid][1] = make_float4(st.z * f, st.z * f, st.w * f, st.w * f);
+            S.St[tid] = make_float4(st.x * f, st.y * f, st.z * f, st.w * f);
             S.Gf[tid] = S.rG[tid].w;
+            ext = S.rG[tid].w != 0.f;
         }
-        __syncthreads();
+        // the chunk has an extended source if any thread saw one
+        ext = __syncthreads_or(ext) != 0;
         if (s0 + SC < se) issue(s0 + SC);
+        if (s0 == sb) {
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int a = role == 2 ? tl.p + ((tl.fold + 4 * r) & 7) : min(tl.p + r, nloc - 1);
+                const float2 x = S.uv[role == 0 ? 0 : a];
+                up[r] = f2(x.x, x.x);
+                vp[r] = f2(x.y, x.y);
+            }
+        }
 
         // ---- source sum for this thread's baselines (Algorithm 2) ----
         if (role == 1) {
             const int ip = apad(tl.p), iq = apad(tl.q);
-            const float2 uvp = S.uv[tl.p];
-            const float2 up = f2(uvp.x, uvp.x), vp = f2(uvp.y, uvp.y);
-#pragma unroll 1
-            for (int s = 0; s < sc; s++) {
-                const float4 s01 = S.St[s][0], s23 = S.St[s][1];
-                const float axs = S.Kx[s * RSTR + ip], ays = S.Ky[s * RSTR + ip];
-                const float2 ax = f2(axs, axs), ay = f2(ays, ays);
-                const float4 *bxv = reinterpret_cast<const float4 *>(KxC + s * cstr + iq);
-                const float4 *byv = reinterpret_cast<const float4 *>(KyC + s * cstr + iq);
-                const float4 bx01 = bxv[0], bx23 = bxv[1], by01 = byv[0], by23 = byv[1];
-                const float2 bx[4] = {f2(bx01.x, bx01.y), f2(bx01.z, bx01.w), f2(bx23.x, bx23.y), f2(bx23.z, bx23.w)};
-                const float2 by[4] = {f2(by01.x, by01.y), f2(by01.z, by01.w), f2(by23.x, by23.y), f2(by23.z, by23.w)};
-                if (S.Gf[s] != 0.f) {
-                    const bool disk = S.Gf[s] > 1.5f;
-                    const float qps = S.Qr[s * RSTR + ip];
-                    const float2 qp = f2(qps, qps);
-                    const float4 *qv = reinterpret_cast<const float4 *>(QC + s * cstr + iq);
-                    const float4 *lxv = reinterpret_cast<const float4 *>(LxC + s * cstr + iq);
-                    const float4 *lyv = reinterpret_cast<const float4 *>(LyC + s * cstr + iq);
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float4 q4 = qv[h], lx4 = lxv[h], ly4 = lyv[h];
-                        const float2 g0 = shape2<GENERAL>(disk, qp, up, vp, f2(q4.x, q4.y), f2(lx4.x, lx4.y),
-                                                          f2(ly4.x, ly4.y));
-                        const float2 g1 = shape2<GENERAL>(disk, qp, up, vp, f2(q4.z, q4.w), f2(lx4.z, lx4.w),
-                                                          f2(ly4.z, ly4.w));
-                        const float2 nax = f2(-ax.x, -ax.y);
-                        const float2 zr0 = __fmul2_rn(__ffma2_rn(ax, bx[2 * h], __fmul2_rn(ay, by[2 * h])), g0);
-                        const float2 zi0 = __fmul2_rn(__ffma2_rn(ay, bx[2 * h], __fmul2_rn(nax, by[2 * h])), g0);
-                        const float2 zr1 = __fmul2_rn(__ffma2_rn(ax, bx[2 * h + 1], __fmul2_rn(ay, by[2 * h + 1])), g1);
-                        const float2 zi1 = __fmul2_rn(__ffma2_rn(ay, bx[2 * h + 1], __fmul2_rn(nax, by[2 * h + 1])), g1);
-                        const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
-#pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            acc[2 * h].re[c] = __ffma2_rn(zr0, X[c], acc[2 * h].re[c]);
-                            acc[2 * h + 1].re[c] = __ffma2_rn(zr1, X[c], acc[2 * h + 1].re[c]);
-                            acc[2 * h].im[c] = __ffma2_rn(zi0, X[c], acc[2 * h].im[c]);
-                            acc[2 * h + 1].im[c] = __ffma2_rn(zi1, X[c], acc[2 * h + 1].im[c]);
-                        }
-                    }
-                } else {
-#pragma unroll
-                    {
-                        float2 zr[4], zi[4];
-                        const float2 nax = f2(-ax.x, -ax.y);
-#pragma unroll
-                        for (int h = 0; h < 4; h++) {
-                            zr[h] = __ffma2_rn(ax, bx[h], __fmul2_rn(ay, by[h]));
-                            zi[h] = __ffma2_rn(ay, bx[h], __fmul2_rn(nax, by[h]));
-                        }
-                        const float2 X[4] = {f2(s01.x, s01.y), f2(s01.z, s01.w), f2(s23.x, s23.y), f2(s23.z, s23.w)};
-#pragma unroll
-                        for (int c = 0; c < 4; c++)
-#pragma unroll
-                            for (int h = 0; h < 4; h++) {
-                                acc[h].re[c] = __ffma2_rn(zr[h], X[c], acc[h].re[c]);
-                                acc[h].im[c] = __ffma2_rn(zi[h], X[c], acc[h].im[c]);
-                            }
-                    }
-                }
-            }
+            if (ext) body_chunk<true, GENERAL>(acc, S, KxC, KyC, QC, LxC, LyC, cstr, ip, iq, sc, up, vp);
+            else body_chunk<false, GENERAL>(acc, S, KxC, KyC, QC, LxC, LyC, cstr, ip, iq, sc, up, vp);
         } else if (role == 2) {
-            const int hb = apad(tl.p), r = tl.fold;
-            int ho[8];   // shared-memory offsets of x_0..x_7 (one 8-antenna block)
-#pragma unroll
-            for (int i = 0; i < 8; i++) ho[i] = hb + ((r + i) & 7);
-            const float2 uv0 = S.uv[tl.p + (r & 7)], uv4 = S.uv[tl.p + ((r + 4) & 7)];
-            // rows of the four slot pairs: (x0, x0), (x0, x0), (x4, x4), (x4, x4)
-            const float2 up[2] = {f2(uv0.x, uv0.x), f2(uv4.x, uv4.x)};
-            const float2 vp[2] = {f2(uv0.y, uv0.y), f2(uv4.y, uv4.y)};
-#pragma unroll 1
-            for (int s = 0; s < sc; s++) {
-                const float4 s01 = S.St[s][0], s23 = S.St[s][1];
-                const float *kx = S.Kx + s * RSTR, *ky = S.Ky + s * RSTR;
-                const float2 ax[2] = {f2(kx[ho[0]], kx[ho[0]]), f2(kx[ho[4]], kx[ho[4]])};
-                const float2 ay[2] = {f2(ky[ho[0]], ky[ho[0]]), f2(ky[ho[4]], ky[ho[4]])};
-                const bool is_gauss = S.Gf[s] != 0.f, disk = S.Gf[s] > 1.5f;
-                const float *qq = S.Qr + s * RSTR, *lx = S.Lxr + s * RSTR, *ly = S.Lyr + s * RSTR;
-#pragma unroll
-                for (int h = 0; h < 4; h++) {
-                    const int r2 = h < 2 ? 0 : 1;
-                    const int c0 = ho[2 * h + 1], c1 = h < 3 ? ho[2 * h + 2] : ho[0];   // slot 7 unused
-                    const float2 bx = f2(kx[c0], kx[c1]), by = f2(ky[c0], ky[c1]);
-                    if (is_gauss) {
-                        const float qps = qq[ho[4 * r2]];
-                        const float2 g = shape2<GENERAL>(disk, f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]),
-                                                f2(lx[c0], lx[c1]), f2(ly[c0], ly[c1]));
-                        accumulate2g(acc[h], ax[r2], ay[r2], bx, by, g, s01, s23);
-                    } else {
-                        accumulate2(acc[h], ax[r2], ay[r2], bx, by, s01, s23);
-                    }
-                }
-            }
+            if (ext) head_chunk<true, GENERAL>(acc, S, tl, sc, up, vp);
+            else head_chunk<false, GENERAL>(acc, S, tl, sc, up, vp);
         }
     }
 
@@ -632,7 +632,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         __syncthreads();
     }
     const float2 I2[4] = {f2(1.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(1.f, 0.f)};
-    float gpsum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // gradient mode, body tiles
+    float gpsum[2][8] = {};   // gradient mode, body tiles: the two row antennas
 #pragma unroll
     for (int j = 0; j < NSLOT; j++) {
         if (!((mask >> j) & 1u)) continue;
@@ -697,9 +697,9 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 if (P.grad_gains) {
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
-                        if (role == 1) {        // body tile: one row antenna for every slot
-                            gpsum[2 * c] += dGp[c].x;
-                            gpsum[2 * c + 1] += dGp[c].y;
+                        if (role == 1) {        // body tile: row p for slots 0-3, p + 1 for 4-7
+                            gpsum[j >> 2][2 * c] += dGp[c].x;
+                            gpsum[j >> 2][2 * c + 1] += dGp[c].y;
                         } else {
                             atomicAdd(&S.GG[lp * 8 + 2 * c], dGp[c].x);
                             atomicAdd(&S.GG[lp * 8 + 2 * c + 1], dGp[c].y);
@@ -712,9 +712,12 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         }
     }
     if constexpr (GRAD) {
-        if (P.grad_gains && role == 1 && mask)
+        if (P.grad_gains && role == 1)
 #pragma unroll
-            for (int c = 0; c < 8; c++) atomicAdd(&S.GG[tl.p * 8 + c], gpsum[c]);
+            for (int r = 0; r < 2; r++)
+                if (mask & (0xfu << (4 * r)))
+#pragma unroll
+                    for (int c = 0; c < 8; c++) atomicAdd(&S.GG[(tl.p + r) * 8 + c], gpsum[r][c]);
         __syncthreads();
         for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
             const int la = i >> 3;
@@ -836,12 +839,13 @@ static bool emit_units(int na, int precision, Sink &sink) {
     for (int r0 = 0; r0 < na; r0 += ROWS) {
         int nr = std::min(ROWS, na - r0);
         int nblk = (nr + 7) / 8;
-        // diagonal unit: body tiles (p, 8g) for groups g past p's own 8-block,
-        // then 4 head tiles per 8-block for the pairs inside the block
+        // diagonal unit: 2 x 4 body tiles (rows p, p + 1; columns q .. q + 3)
+        // for column blocks past the rows' own 8-block, then 4 head tiles per
+        // 8-block for the pairs inside the block
         Unit d{r0, r0, nr, nr, ntile, 0, 0, 1};
-        for (int p = 0; p < nr; p++)
-            for (int g = p / 8 + 1; g < nblk; g++)
-                if (!tile(p, 8 * g, 0)) return false;
+        for (int p = 0; p < nr; p += 2)
+            for (int q = 8 * (p / 8 + 1); q < nr; q += 4)
+                if (!tile(p, q, 0)) return false;
         d.nbody = ntile - d.tile0;
         for (int f = 0; f < 4; f++)
             for (int m = 0; m < nblk; m++)
@@ -851,9 +855,9 @@ static bool emit_units(int na, int precision, Sink &sink) {
         for (int c0 = r0 + ROWS; c0 < na; c0 += COLS) {
             int nc = std::min(COLS, na - c0);
             Unit o{r0, c0, nr, nc, ntile, 0, 0, 0};
-            for (int p = 0; p < nr; p++)
-                for (int g = 0; 8 * g < nc; g++)
-                    if (!tile(p, 8 * g, 0)) return false;
+            for (int p = 0; p < nr; p += 2)
+                for (int q = 0; q < nc; q += 4)
+                    if (!tile(p, q, 0)) return false;
             o.nbody = ntile - o.tile0;
             if (!sink.unit(o)) return false;
         }

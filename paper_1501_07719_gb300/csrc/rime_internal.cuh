@@ -123,6 +123,7 @@ struct FusedParams {
     double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
     int src0, src1;            // the source range [src0, src1) of this launch (default: all)
     int t_begin;               // first timestep of the launch (the grid covers a time range)
+    float *segsum;             // FP32 tile kernel, long source lists: per-block running sums
 };
 
 // Batched chi^2: the schedule of a persistent launch. Work item i is
@@ -224,6 +225,10 @@ struct rime_ctx {
     std::vector<BatchTune> btuned;    // tuned configurations by (nsets, total sources)
     int bmax_bps = 0;                 // resident batched blocks per SM (0: not queried yet)
     int nsm = 0;
+    unsigned long long wait_ns = 0;   // limit of the kernels' bounded waits (0: about two seconds)
+    float *d_segsum = nullptr;        // FP32 tile kernel: running sums of long source lists, per block
+    size_t segsum_blocks = 0;         // blocks it holds
+    bool view = false;                // a view over caller memory (rime_chi2_noalloc): allocates nothing
     // tensor-core split-precision mode (FP32 contexts)
     int tc_mode = 0;                  // rime_tc_mode
     int kernel = 0;                   // rime_kernel

@@ -115,6 +115,7 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     if (nunits <= 0) return fail(RIME_E_INVALID, "rime_chi2_noalloc: work-unit table does not fit");
 
     rime_ctx c;   // a view over the caller's arrays and the scratch; owns nothing
+    c.view = true;
     c.dims = *dims;
     c.nbl = rime_nbl(dims->na);
     c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
