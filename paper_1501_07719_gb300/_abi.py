@@ -255,7 +255,17 @@ def rime_destroy(ctx):
 def rime_chi2_noalloc(na, ntime, nchan, precision, freq_hz, uvw, pointing, data, weight, gains,
                       lm, stokes, alpha, shape, chi2_dev, stream=0, ref_freq_hz=1.4e9, beam_c=65.0, kind=None):
     """The chi^2 entry point that allocates no device memory (see include/rime.h).
-    Every array argument must be a device tensor; chi2_dev receives the value."""
+    Every array argument must be a CUDA tensor on the current device (or None
+    where the ABI allows NULL); chi2_dev receives the value."""
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    named = dict(freq_hz=freq_hz, uvw=uvw, pointing=pointing, data=data, weight=weight, gains=gains,
+                 lm=lm, stokes=stokes, alpha=alpha, shape=shape, kind=kind, chi2_dev=chi2_dev)
+    for name, x in named.items():
+        if x is None:
+            continue
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.device.index != dev:
+            raise TypeError(f"rime_chi2_noalloc: {name} must be a CUDA tensor on the current device (cuda:{dev})")
     cd, rd = _ctype(precision)
     k = _Keep()
     dims = rime_dims(na, ntime, nchan, precision, ref_freq_hz, beam_c)

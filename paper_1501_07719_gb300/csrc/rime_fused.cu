@@ -288,8 +288,11 @@ namespace f32 {
 #ifndef RIME_F32_MIN_BLOCKS
 #define RIME_F32_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
 #endif
+#ifndef RIME_F32_SC
+#define RIME_F32_SC 20          // sources per staged chunk
+#endif
 constexpr int THREADS = 256;
-constexpr int SC = 16;               // sources per chunk
+constexpr int SC = RIME_F32_SC;      // sources per chunk
 constexpr int ROWS = 64, COLS = 32;  // unit shape (off-diagonal: 64 x 32)
 constexpr int NLOC = ROWS + COLS;    // antennas staged per unit, at most
 constexpr int RSTR = 96;             // staged row of a per-antenna quantity: 64 antennas, 4 pad per 8
@@ -394,11 +397,20 @@ __device__ __forceinline__ float2 shape2(bool disk, float2 qp, float2 up, float2
 
 // One chunk of sources for a 2 x 4 body tile (rows at ip, columns at iq of
 // the staged rows; cstr the column rows' stride).
+#ifndef RIME_F32_UNROLL_PT
+#define RIME_F32_UNROLL_PT 1    // unrolling of the body tiles' point-source loop
+#endif
+#ifndef RIME_F32_UNROLL_EXT
+#define RIME_F32_UNROLL_EXT 1   // ... and of their loop with shape factors
+#endif
+#define RIME_PRAGMA(x) _Pragma(#x)
+#define RIME_UNROLL(n) RIME_PRAGMA(unroll n)
 template <bool SHAPE, bool GENERAL>
 __device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const float *KxC, const float *KyC,
                                            const float *QC, const float *LxC, const float *LyC, int cstr, int ip,
                                            int iq, int sc, float2 (&up)[2], float2 (&vp)[2]) {
-#pragma unroll 1
+    constexpr int UNR = SHAPE ? RIME_F32_UNROLL_EXT : RIME_F32_UNROLL_PT;
+    RIME_UNROLL(UNR)
     for (int s = 0; s < sc; s++) {
         const float2 kr = *reinterpret_cast<const float2 *>(S.Kx + s * RSTR + ip);
         const float2 ki = *reinterpret_cast<const float2 *>(S.Ky + s * RSTR + ip);
@@ -472,7 +484,50 @@ __device__ __forceinline__ void head_chunk(Pair (&acc)[NSLOT / 2], const Smem &S
 // the exponential disks too. The kernel runs at its register limit: a
 // run-time choice (the Bessel function's code beside cos^3 in the staging
 // loop) cost the common case 1.5 %.
-template <int MODE, bool GENERAL>
+// Long source lists: every SEG sources the thread's 64 FP32 sums are added
+// into running sums in a per-block scratch (a second FP32 set would not fit
+// the registers) with the rounding error of each addition kept in a low part
+// (two-sum), and restart at zero; so no FP32 sum runs over more than SEG terms
+// (4096 sequential FP32 additions at |V| ~ 1e2 Jy would round away more than
+// the chi^2 of a 0.01 Jy residual tolerates). Scratch layout per block:
+// [hi | lo][64][THREADS] floats.
+constexpr int SEG = 240;
+__device__ __forceinline__ float *seg_base(const FusedParams &P) {
+    return P.segsum + (size_t)blockIdx.x * 2 * 64 * THREADS + threadIdx.x;
+}
+template <typename F>
+__device__ __forceinline__ void each_sum(Pair (&acc)[NSLOT / 2], F &&f) {
+#pragma unroll
+    for (int h = 0; h < NSLOT / 2; h++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            f(16 * h + 4 * c + 0, acc[h].re[c].x);
+            f(16 * h + 4 * c + 1, acc[h].re[c].y);
+            f(16 * h + 4 * c + 2, acc[h].im[c].x);
+            f(16 * h + 4 * c + 3, acc[h].im[c].y);
+        }
+}
+__device__ __forceinline__ void fold_segment(const FusedParams &P, Pair (&acc)[NSLOT / 2], bool held) {
+    float *hi = seg_base(P), *lo = hi + 64 * THREADS;
+    each_sum(acc, [&](int f, float &v) {
+        if (!held) {
+            hi[f * THREADS] = v;
+            lo[f * THREADS] = 0.f;
+        } else {
+            const float h = hi[f * THREADS];
+            const float sm = h + v, bb = sm - h;
+            lo[f * THREADS] += (h - (sm - bb)) + (v - bb);
+            hi[f * THREADS] = sm;
+        }
+        v = 0.f;
+    });
+}
+__device__ __forceinline__ void unfold_segments(const FusedParams &P, Pair (&acc)[NSLOT / 2]) {
+    const float *hi = seg_base(P), *lo = hi + 64 * THREADS;
+    each_sum(acc, [&](int f, float &v) { v = hi[f * THREADS] + (lo[f * THREADS] + v); });
+}
+
+template <int MODE, bool GENERAL, bool SEGD = false>
 __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se) {
     constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     const int tid = threadIdx.x;
@@ -551,6 +606,8 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
     // the rows' antenna coordinates, as pairs (filled after the first barrier)
     float2 up[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, vp[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+    int nacc = 0;        // sources in the current register segment (long lists)
+    bool held = false;   // earlier segments are in the running sums
 
     for (int s0 = sb; s0 < se; s0 += SC) {
         const int sc = min(SC, se - s0);
@@ -619,7 +676,17 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             if (ext) head_chunk<true, GENERAL>(acc, S, tl, sc, up, vp);
             else head_chunk<false, GENERAL>(acc, S, tl, sc, up, vp);
         }
+        if constexpr (SEGD) {
+            nacc += sc;
+            if (nacc >= SEG && s0 + SC < se) {
+                fold_segment(P, acc, held);
+                held = true;
+                nacc = 0;
+            }
+        }
     }
+    if constexpr (SEGD)
+        if (held) unfold_segments(P, acc);
 
     // ---- epilogue: S (eq. 2), gains (eq. 1), chi^2 terms (eq. 7) ----
     float chi = 0.f;
@@ -748,6 +815,42 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int t = P.t_begin + rest / P.nchan;
     const double bsum = fused_item<MODE, GENERAL>(P, S, t, k, u, P.src0, P.src1);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
+}
+
+// Long source lists: a persistent grid (its blocks' running sums fit a
+// scratch of one slot per block) over the items of k_fused_f32; one partial
+// per item at the item's index, the last block adds them in index order.
+template <int MODE, bool GENERAL>
+__global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32_seg(const FusedParams P, long long nitems) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    __shared__ int sLast;
+    if (inputs_bad(P.status)) return;
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        __syncthreads();   // the previous item is done with the shared buffers
+        const int u = (int)(item % P.nunits);
+        const long long rest = item / P.nunits;
+        const int k = (int)(rest % P.nchan);
+        const int t = P.t_begin + (int)(rest / P.nchan);
+        const double bsum = fused_item<MODE, GENERAL, true>(P, S, t, k, u, P.src0, P.src1);
+        if (MODE != MODE_PREDICT && threadIdx.x == 0) P.partials[item] = bsum;
+    }
+    if constexpr (MODE == MODE_PREDICT) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(P.counter, 1u);
+        sLast = ticket == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!sLast) return;
+    __threadfence();
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < nitems; i += THREADS) s += __ldcg(&P.partials[i]);
+    const double tot = block_sum<THREADS>(s, S.red);
+    if (threadIdx.x == 0) {
+        *P.result = tot;
+        *P.counter = 0u;
+    }
 }
 
 // Batched chi^2: many source sets against one observation in one persistent
@@ -953,6 +1056,40 @@ cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *resu
     return launch_tiled_params(c, mode, P, fused_blocks(c));
 }
 
+long long seg_source_threshold() { return 2 * f32::SEG; }
+size_t seg_scratch_per_block() { return (size_t)2 * 64 * f32::THREADS * sizeof(float); }
+
+// Long source lists (FP32): the persistent kernel with per-block running sums.
+static cudaError_t launch_seg_f32(rime_ctx *c, int mode, const FusedParams &P, long long nitems, cudaStream_t stream) {
+    const size_t per_block = seg_scratch_per_block();
+    if (c->nsm <= 0 && cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->nsm = 152;
+    if (!c->d_segsum && !c->view) {
+        Alloc alloc{c};
+        const size_t nb = (size_t)c->nsm * RIME_F32_MIN_BLOCKS;
+        cudaError_t e = alloc((void **)&c->d_segsum, per_block * nb);
+        if (e != cudaSuccess) return e;
+        c->segsum_blocks = nb;
+    }
+    if (!c->d_segsum || c->segsum_blocks == 0) return cudaErrorInvalidValue;
+    FusedParams Q = P;
+    Q.segsum = c->d_segsum;
+    const long long grid = std::min<long long>(nitems, (long long)c->segsum_blocks);
+    const size_t sm = sizeof(f32::Smem);
+    auto go = [&](auto kernel) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        kernel<<<(unsigned)grid, f32::THREADS, sm, stream>>>(Q, nitems);
+        return cudaGetLastError();
+    };
+    const bool general = c->beam_model != RIME_BEAM_COS3 || c->has_kind;
+    switch (mode) {
+        case MODE_PREDICT: return general ? go(f32::k_fused_f32_seg<MODE_PREDICT, true>) : go(f32::k_fused_f32_seg<MODE_PREDICT, false>);
+        case MODE_CHI2: return general ? go(f32::k_fused_f32_seg<MODE_CHI2, true>) : go(f32::k_fused_f32_seg<MODE_CHI2, false>);
+        default: return general ? go(f32::k_fused_f32_seg<MODE_GRAD, true>) : go(f32::k_fused_f32_seg<MODE_GRAD, false>);
+    }
+}
+
 cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long nblocks, cudaStream_t stream) {
     if (!stream) stream = c->stream;
     if (nblocks == 0) return cudaSuccess;
@@ -967,6 +1104,7 @@ cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, lon
         }
     }
     size_t sm = sizeof(f32::Smem);
+    if (P.src1 - P.src0 > seg_source_threshold()) return launch_seg_f32(c, mode, P, nblocks, stream);
     if (c->beam_model != RIME_BEAM_COS3 || c->has_kind) switch (mode) {
             case MODE_PREDICT: return launch_k(f32::k_fused_f32<MODE_PREDICT, true>, P, blocks, f32::THREADS, sm, stream);
             case MODE_CHI2: return launch_k(f32::k_fused_f32<MODE_CHI2, true>, P, blocks, f32::THREADS, sm, stream);

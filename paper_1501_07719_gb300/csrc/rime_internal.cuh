@@ -295,6 +295,10 @@ cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid);
 int batched_blocks_per_sm();
 cudaError_t launch_set_sums(rime_ctx *c, int nsets, int per_set, const double *partials, double *chi2);
 cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *result);
+// FP32 source lists longer than this run the persistent kernel with per-block
+// running sums of this many bytes per block (rime_fused.cu)
+long long seg_source_threshold();
+size_t seg_scratch_per_block();
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
                        double *grad_gains);
 // launches the tiled fused kernel of `mode` with prepared parameters over `blocks` blocks

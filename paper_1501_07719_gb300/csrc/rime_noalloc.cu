@@ -13,6 +13,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <mutex>
 
 using namespace rime;
@@ -21,8 +22,9 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(32) << 20;   // 32 MiB
 constexpr int kMaxNaNoAlloc = 256;                    // bounds the unit table below
-constexpr int kMaxUnits = 64;
-constexpr int kMaxTiles = kMaxUnits * 288;
+// at 256 antennas: 16 units (FP32) or 36 (FP64), at most 256 thread tiles each
+constexpr int kMaxUnits = 40;
+constexpr int kMaxTiles = kMaxUnits * 256;
 
 // The scratch shared by every call in this process on a given device.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -108,14 +110,38 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     if (src->nsrc > 0 && (!src->lm || !src->stokes || !src->alpha))
         return fail(RIME_E_INVALID, "lm, stokes and alpha must not be NULL when nsrc > 0");
 
+    // every argument array must be device memory of the current device (or
+    // managed memory): the kernels read them as they are
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(RIME_E_CUDA, "rime_chi2_noalloc: no current device");
+    const void *ptrs[] = {freq_hz, uvw, pointing, data, weight, gains, src->lm, src->stokes, src->alpha,
+                          src->shape, src->kind, chi2_dev};
+    const char *names[] = {"freq_hz", "uvw", "pointing", "data", "weight", "gains", "lm", "stokes", "alpha",
+                           "shape", "kind", "chi2_dev"};
+    for (int i = 0; i < 12; i++) {
+        if (!ptrs[i]) continue;
+        if (i >= 6 && i <= 10 && src->nsrc == 0) continue;   // source arrays are not read
+        if (i == 10 && !src->shape) continue;                // kind is read only with a shape
+        cudaPointerAttributes a;
+        const bool known = cudaPointerGetAttributes(&a, ptrs[i]) == cudaSuccess;
+        if (!known) cudaGetLastError();   // clear the error of an unregistered host pointer
+        const bool ok = known && (a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev));
+        if (!ok) {
+            char buf[160];
+            std::snprintf(buf, sizeof buf, "rime_chi2_noalloc: %s is not device memory of the current device", names[i]);
+            return fail(RIME_E_INVALID, buf);
+        }
+    }
+
     Unit units[kMaxUnits];
-    Tile tiles[kMaxTiles];   // 36 KB on the stack
+    Tile tiles[kMaxTiles];   // 40 KB on the caller's stack
     int ntiles = 0;
     int nunits = build_units_fixed(dims->na, dims->precision, units, kMaxUnits, tiles, kMaxTiles, &ntiles);
     if (nunits <= 0) return fail(RIME_E_INVALID, "rime_chi2_noalloc: work-unit table does not fit");
 
     rime_ctx c;   // a view over the caller's arrays and the scratch; owns nothing
     c.view = true;
+    c.device = dev;
     c.dims = *dims;
     c.nbl = rime_nbl(dims->na);
     c.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -141,6 +167,18 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     size_t o_units = L.take((size_t)nunits * sizeof(Unit));
     size_t o_tiles = L.take((size_t)ntiles * sizeof(Tile));
     size_t o_part = L.take(blocks * sizeof(double));
+    // long FP32 source lists: the running sums of the persistent kernel's
+    // blocks, as many blocks as the rest of the array holds (at most two per SM)
+    size_t o_seg = 0, nseg = 0;
+    if (dims->precision == RIME_FP32 && (long long)nsrc > seg_source_threshold()) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+        const size_t per = seg_scratch_per_block();
+        const size_t room = L.off < kScratchBytes ? (kScratchBytes - L.off) / per : 0;
+        nseg = std::min((size_t)2 * nsm, room);
+        if (nseg == 0) nseg = 1;   // reported below as too large
+        o_seg = L.take(nseg * per);
+    }
     if (L.off > kScratchBytes) {
         char buf[200];
         std::snprintf(buf, sizeof buf,
@@ -182,6 +220,10 @@ extern "C" rime_status rime_chi2_noalloc(const rime_dims *dims, const double *fr
     c.d_tiles = reinterpret_cast<Tile *>(base + o_tiles);
     c.d_partials = reinterpret_cast<double *>(base + o_part);
     c.partials_cap = blocks;
+    if (nseg) {
+        c.d_segsum = reinterpret_cast<float *>(base + o_seg);
+        c.segsum_blocks = nseg;
+    }
     c.nsrc = (int)nsrc;
     c.time_varying = src->time_varying;
     c.has_shape = src->shape != nullptr;

@@ -52,6 +52,12 @@ CASES = {
                         time_varying=True),
     "70ant-disks-jinc": dict(wl=rime_synth.custom(70, 2, 3, 6, 11, seed_index=40), disk_fraction=0.5,
                              pointing_sigma=0.002, **JINC),
+    # long source lists: the FP32 tiled kernel's per-block running sums (more
+    # than two register segments of 240 sources), across units, pointing
+    # errors, and with the general instance (Jinc beam, disks)
+    "70ant-long": dict(wl=rime_synth.custom(70, 2, 2, 330, 250, seed_index=41), pointing_sigma=0.002),
+    "40ant-long-jinc-disks": dict(wl=rime_synth.custom(40, 2, 2, 300, 300, seed_index=42), disk_fraction=0.5,
+                                  **JINC),
 }
 
 
@@ -164,6 +170,36 @@ def test_full_64ant_workload_sampled_fp32():
     r.close()
     del V
     torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def full_64ant():
+    """The benchmark's 64-antenna, 100-timestep, 64-channel, 100 point + 100
+    Gaussian workload with data = the oracle's model + the seeded noise, every
+    input rounded to FP32 (so that the same values serve the FP32 and the FP64
+    runs), and the oracle's chi^2 of it."""
+    inp = rime_synth.make_inputs("64ant-100t-64ch-100pt100g", precision="f32")
+    V = oracle.Problem(inp).predict()
+    inp["data"] = rime_synth.observe(V, inp["noise"], "f32")
+    del V
+    inp["want_chi2"] = oracle.Problem(inp, data=inp["data"]).chi2()
+    return inp
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_full_64ant_chi2_against_oracle(full_64ant, precision):
+    """rime_chi2 of the whole benchmark workload, in the benchmark's launch
+    configuration, against the FP64 oracle's chi^2 of the same inputs."""
+    import paper_1501_07719_gb300 as R
+    inp = full_64ant
+    prec = R.RIME_FP32 if precision == "f32" else R.RIME_FP64
+    cd, rd = (np.complex64, np.float32) if precision == "f32" else (np.complex128, np.float64)
+    r = R.Rime(inp, prec, data=inp["data"].astype(cd), weight=inp["weight"].astype(rd))
+    r.set_gains(inp["gains"])
+    r.set_sources(inp["sources"])
+    got = r.chi2()
+    r.close()
+    assert rel_err(got, inp["want_chi2"]) <= TOL[precision]["chi2"], (got, inp["want_chi2"])
 
 
 def test_invalid_source_is_reported_and_outputs_untouched():
