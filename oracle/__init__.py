@@ -48,6 +48,7 @@ def lib():
         L.rime_oracle_ln_norm.argtypes = [C.POINTER(_Problem)]
         L.rime_oracle_ln_norm.restype = C.c_double
         L.rime_oracle_threads.restype = C.c_int
+        L.rime_oracle_reduced_phase.argtypes = [C.c_long, _dp, _dp, _dp]
         _lib = L
     return _lib
 
@@ -143,3 +144,12 @@ class Problem:
 
 def threads() -> int:
     return lib().rime_oracle_threads()
+
+
+def reduced_phase(nu, tau) -> np.ndarray:
+    """nu tau - round(nu tau) in turns (eq. 3's phase modulo whole turns), FP64."""
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    out = np.zeros(nu.shape)
+    lib().rime_oracle_reduced_phase(int(nu.size), _ptr(nu), _ptr(tau), _ptr(out))
+    return out

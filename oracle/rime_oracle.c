@@ -472,6 +472,16 @@ double rime_oracle_chi2_grad(const rime_oracle_problem *P, double *grad_src,
     return nsum_get(&chi);
 }
 
+/* eq. 3: K = exp(2 pi i nu tau) depends on nu tau only through its
+ * remainder modulo whole turns; this is that remainder, nearest integer
+ * removed (the definition, in FP64). */
+void rime_oracle_reduced_phase(long n, const double *nu, const double *tau, double *out) {
+    for (long i = 0; i < n; i++) {
+        const double x = nu[i] * tau[i];
+        out[i] = x - nearbyint(x);
+    }
+}
+
 int rime_oracle_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

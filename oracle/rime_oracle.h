@@ -62,6 +62,10 @@ double rime_oracle_chi2_grad(const rime_oracle_problem *P, double *grad_src,
 /* The likelihood constant sum ln(2 pi / w) over all visibilities (eq. 7). */
 double rime_oracle_ln_norm(const rime_oracle_problem *P);
 
+/* The phase of eq. 3 in turns, nu tau, reduced to nu tau - round(nu tau)
+ * (nearest integer, ties to even), for n pairs. */
+void rime_oracle_reduced_phase(long n, const double *nu, const double *tau, double *out);
+
 /* Number of threads the parallel loops use. */
 int rime_oracle_threads(void);
 

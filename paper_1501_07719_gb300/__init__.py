@@ -8,7 +8,8 @@ from ._abi import (RIME_BEAM_COS3, RIME_BEAM_JINC, RIME_FP32, RIME_FP64, RIME_KE
                    rime_batched_config, rime_chains_accept, rime_chains_init, rime_chains_propose, rime_chi2, rime_chi2_async, rime_chi2_batched, rime_chi2_grad,
                    rime_chi2_noalloc, rime_chi2_streamed, rime_create, rime_destroy, rime_last_error, rime_ln_norm, rime_nbl,
                    rime_predict, rime_set_batched_config, rime_set_data, rime_set_gains, rime_set_sources,
-                   rime_set_beam, rime_set_kernel, rime_set_tensor_mode, rime_set_uvw, rime_sync)
+                   rime_set_beam, rime_set_kernel, rime_set_tensor_mode, rime_set_uvw, rime_set_wait_limit, rime_sync,
+                   rime_phase_turns)
 from .context import Rime
 from .autograd import RimeChi2
 
@@ -17,4 +18,5 @@ __all__ = ["RIME_BEAM_COS3", "RIME_BEAM_JINC", "RIME_FP32", "RIME_FP64", "RIME_K
            "rime_chains_propose", "rime_chi2", "rime_chi2_async", "rime_chi2_batched",
            "rime_chi2_grad", "rime_chi2_noalloc", "rime_chi2_streamed", "rime_create", "rime_destroy", "rime_last_error", "rime_ln_norm",
            "rime_nbl", "rime_predict", "rime_set_batched_config", "rime_set_data", "rime_set_gains",
-           "rime_set_beam", "rime_set_kernel", "rime_set_sources", "rime_set_tensor_mode", "rime_set_uvw", "rime_sync"]
+           "rime_set_beam", "rime_set_kernel", "rime_set_sources", "rime_set_tensor_mode", "rime_set_uvw",
+           "rime_set_wait_limit", "rime_sync", "rime_phase_turns"]

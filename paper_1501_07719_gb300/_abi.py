@@ -78,12 +78,14 @@ def lib():
         L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
         L.rime_set_kernel.argtypes = [vp, C.c_int32]
+        L.rime_set_wait_limit.argtypes, L.rime_set_wait_limit.restype = [vp, C.c_uint64], ip
         L.rime_set_beam.argtypes = [vp, C.c_int32, C.c_double]
         L.rime_chains_init.argtypes = [vp, C.c_int32]
         L.rime_chains_propose.argtypes = [vp, C.c_int32, C.POINTER(rime_sources), C.POINTER(rime_sources), vp]
         L.rime_chains_accept.argtypes = [vp, vp]
         L.rime_chi2_streamed.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
         L.rime_stream_chunk_ntime.argtypes, L.rime_stream_chunk_ntime.restype = [vp], C.c_int32
+        L.rime_phase_turns.argtypes, L.rime_phase_turns.restype = [C.c_int64, vp, vp, vp], ip
         for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
                   "rime_set_kernel", "rime_chi2_streamed", "rime_set_beam", "rime_chains_init",
                   "rime_chains_propose", "rime_chains_accept"):
@@ -361,3 +363,19 @@ def rime_set_kernel(ctx, kernel: int):
 def rime_set_tensor_mode(ctx, mode: int):
     """RIME_TC_OFF, RIME_TC_SPLIT_BF16 or RIME_TC_SPLIT_TF32 (FP32 contexts)."""
     _check(lib().rime_set_tensor_mode(ctx, int(mode)), ctx)
+
+
+def rime_phase_turns(nu_hz, tau_s) -> np.ndarray:
+    """The FP32 kernels' reduced phase of eq. 3 (turns) for host arrays nu_hz, tau_s."""
+    nu = np.ascontiguousarray(nu_hz, dtype=np.float64)
+    tau = np.ascontiguousarray(tau_s, dtype=np.float64)
+    if nu.shape != tau.shape:
+        raise ValueError("nu_hz and tau_s must have the same shape")
+    out = np.zeros(nu.shape, dtype=np.float32)
+    _check(lib().rime_phase_turns(int(nu.size), nu.ctypes.data, tau.ctypes.data, out.ctypes.data), None)
+    return out
+
+
+def rime_set_wait_limit(ctx, ns: int):
+    """Limit (ns) of the tensor-core kernels' bounded waits; 0: the default (about 2 s)."""
+    _check(lib().rime_set_wait_limit(ctx, int(ns)), ctx)

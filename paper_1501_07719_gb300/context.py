@@ -119,6 +119,10 @@ class Rime:
         with its constant C in rad^-1 GHz^-1."""
         A.rime_set_beam(self.ctx, model, beam_c)
 
+    def set_wait_limit(self, ns: int):
+        """Limit (ns) of the tensor-core kernels' bounded waits (0: about 2 s)."""
+        A.rime_set_wait_limit(self.ctx, ns)
+
     def set_kernel(self, kernel: int):
         """Direct-sum kernel: RIME_KERNEL_AUTO (default), RIME_KERNEL_TILED or
         RIME_KERNEL_NARROW (arrays of up to 45 antennas)."""

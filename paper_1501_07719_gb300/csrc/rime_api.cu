@@ -454,6 +454,12 @@ rime_status rime_set_beam(rime_ctx *c, int32_t model, double beam_c) {
     return RIME_OK;
 }
 
+rime_status rime_set_wait_limit(rime_ctx *c, uint64_t ns) {
+    if (!c) return RIME_E_INVALID;
+    c->wait_ns = (unsigned long long)ns;
+    return RIME_OK;
+}
+
 rime_status rime_set_kernel(rime_ctx *c, int32_t kernel) {
     if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
     if (kernel != RIME_KERNEL_AUTO && kernel != RIME_KERNEL_TILED && kernel != RIME_KERNEL_NARROW)

@@ -93,15 +93,24 @@ __device__ __forceinline__ void grad_terms(const T2 *V, const T2 *Sm, const T2 *
 }
 
 namespace f32 {
-// Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay:
-// nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact, the small
-// products add the rest; the result is reduced to about [-1/2, 1/2] turns,
-// where the SFU sine and cosine are accurate to ~2^-21 absolute.
+// The phase of eq. 3 in turns, nu tau, reduced to about [-1/2, 1/2] from the
+// double-float pairs nu = nu_hi + nu_lo and tau = tau.x + tau.y:
+// nu_hi tau_hi = p + e exactly (FMA), p - round(p) is exact (|p| < 2^22),
+// and the small products add the rest. The result differs from the FP64
+// value nu tau - round(nu tau), rounded to FP32, by at most about one unit in
+// the last place of 1/2 (2^-24 turns) plus 2^-47 |nu tau| (the pairs'
+// representation and the small products' rounding).
+__device__ __forceinline__ float reduced_turns(float2 tau, float nu_hi, float nu_lo) {
+    const float p = nu_hi * tau.x;
+    const float e = fmaf(nu_hi, tau.x, -p);
+    const float r = p - round_int_f(p);
+    return r + (e + fmaf(nu_hi, tau.y, nu_lo * tau.x));
+}
+// Phase factor K = exp(2 pi i nu tau) (eq. 3) from the double-float delay,
+// reduced as above; the SFU sine and cosine are accurate to ~2^-21 absolute
+// on [-pi, pi].
 __device__ __forceinline__ float2 phase_factor(float2 tau, const ChanF &ch) {
-    float p = ch.nu_hi * tau.x;
-    float e = fmaf(ch.nu_hi, tau.x, -p);
-    float r = p - round_int_f(p);
-    float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
+    const float f = reduced_turns(tau, ch.nu_hi, ch.nu_lo);
     float sn, cs;
     __sincosf(6.28318530717958648f * f, &sn, &cs);
     return make_float2(cs, sn);

@@ -5,6 +5,9 @@
 // once per upload, so that the FP32 fused kernel runs no FP64 instruction.
 #include "rime_internal.cuh"
 
+#include <algorithm>
+#include "rime_fused_common.cuh"
+
 #include <math.h>
 
 namespace rime {
@@ -318,4 +321,46 @@ cudaError_t launch_ln_norm(rime_ctx *c) {
     return cudaGetLastError();
 }
 
+// The reduced phase of eq. 3 as the FP32 kernels form it, for (nu, tau)
+// pairs split into double-float pairs exactly as k_prep_channels and the
+// delays kernel split them.
+__global__ void k_phase_turns(long long n, const double *nu, const double *tau, float *out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float nh = (float)nu[i], nl = (float)(nu[i] - (double)nh);
+        const float th = (float)tau[i], tl = (float)(tau[i] - (double)th);
+        out[i] = f32::reduced_turns(make_float2(th, tl), nh, nl);
+    }
+}
+
 }  // namespace rime
+
+extern "C" rime_status rime_phase_turns(int64_t n, const double *nu_hz, const double *tau_s, float *turns) {
+    using namespace rime;
+    if (n < 0 || (n > 0 && (!nu_hz || !tau_s || !turns))) {
+        set_global_error("rime_phase_turns: n must be >= 0 and the arrays non-NULL");
+        return RIME_E_INVALID;
+    }
+    if (n == 0) return RIME_OK;
+    double *d = nullptr;
+    const size_t nb = (size_t)n * (2 * sizeof(double) + sizeof(float));
+    cudaError_t e = cudaMalloc((void **)&d, nb);
+    if (e != cudaSuccess) {
+        set_global_error(cudaGetErrorString(e));
+        return RIME_E_OOM;
+    }
+    float *o = reinterpret_cast<float *>(d + 2 * n);
+    e = cudaMemcpy(d, nu_hz, (size_t)n * sizeof(double), cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(d + n, tau_s, (size_t)n * sizeof(double), cudaMemcpyDefault);
+    if (e == cudaSuccess) {
+        const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+        k_phase_turns<<<(unsigned)blocks, 256>>>(n, d, d + n, o);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(turns, o, (size_t)n * sizeof(float), cudaMemcpyDefault);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_global_error(cudaGetErrorString(e));
+        return RIME_E_CUDA;
+    }
+    return RIME_OK;
+}

@@ -45,6 +45,7 @@
 #include "rime_dev.cuh"
 #include "rime_tc.cuh"
 #include "rime_beam.cuh"
+#include "rime_fused_common.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -96,19 +97,13 @@ struct SplitParams {
     unsigned *counter;
     double *result;
     DevStatus *status;
+    unsigned long long wait_ns;   // limit of the bounded waits
 };
 
 // K = exp(2 pi i nu tau) with nu tau reduced exactly to about [-1/2, 1/2]
-// turns in double-float arithmetic, then the SFU sine and cosine.
-__device__ __forceinline__ float2 phase_sfu(float2 tau, const ChanF &ch) {
-    const float p = ch.nu_hi * tau.x;
-    const float e = fmaf(ch.nu_hi, tau.x, -p);
-    const float r = p - round_int_f(p);
-    const float f = r + (e + fmaf(ch.nu_hi, tau.y, ch.nu_lo * tau.x));
-    float sn, cs;
-    __sincosf(6.28318530717958648f * f, &sn, &cs);
-    return make_float2(cs, sn);
-}
+// turns in double-float arithmetic, then the SFU sine and cosine (the same
+// routine as the direct FP32 kernels).
+__device__ __forceinline__ float2 phase_sfu(float2 tau, const ChanF &ch) { return f32::phase_factor(tau, ch); }
 __device__ __forceinline__ float beam_f(float rho, const ChanF &ch) { return beam_E(ch.beam, ch.cnu * rho); }
 
 // (x, y) -> packed hi and lo words: BF16 pairs (x in the low half).
@@ -164,7 +159,7 @@ struct Item {
 struct Cta {
     const SplitParams &P;
     unsigned char *smem;
-    uint64_t *full, *empty, *seg_full, *seg_empty;
+    uint64_t *full, *empty, *seg_full, *seg_empty, *drained;
     int *abort_flag;
     uint32_t tmem;
     int t, k, p0, q0, nstg, nseg;
@@ -191,8 +186,9 @@ __device__ __forceinline__ bool wait_slot(const Cta &C, int it, int lane, Drain 
         // the lanes agree once all have seen it
         if (__all_sync(0xffffffffu, tc::mbar_try_wait_sleep(&C.empty[slot], par, 1000u))) return true;
         maybe_drain();
-        if ((i & 63) == 63 &&
-            __any_sync(0xffffffffu, *(volatile int *)C.abort_flag != 0 || tc::global_ns() - t0 > 2000000000ull))
+        const bool check = C.P.wait_ns < 1000000ull || (i & 63) == 63;
+        if (check &&
+            __any_sync(0xffffffffu, *(volatile int *)C.abort_flag != 0 || tc::global_ns() - t0 > C.P.wait_ns))
             return false;
     }
 }
@@ -300,7 +296,7 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         if (ok && it + 1 < C.nstg) ok = step(it + 1, b1, b0);
     }
     while (ok && nd < C.nseg) {   // the remaining segments
-        const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&C.seg_full[nd & 1], (nd >> 1) & 1, C.abort_flag));
+        const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&C.seg_full[nd & 1], (nd >> 1) & 1, C.abort_flag, P.wait_ns));
         if (!got) ok = false;
         else drain();
     }
@@ -480,12 +476,12 @@ __device__ __forceinline__ void role_mma(const Cta &C) {
     const uint32_t sbase = tc::smem_u32(C.smem);
     for (int it = 0; it < C.nstg; it++) {
         const int g = it / SEG, b = g & 1, first = it % SEG == 0;
-        if (first && g >= 2 && !tc::mbar_wait(&C.seg_empty[b], ((g >> 1) - 1) & 1, C.abort_flag)) {
+        if (first && g >= 2 && !tc::mbar_wait(&C.seg_empty[b], ((g >> 1) - 1) & 1, C.abort_flag, C.P.wait_ns)) {
             *(volatile int *)C.abort_flag = 1;
             break;
         }
         const int slot = it % NST;
-        if (!tc::mbar_wait(&C.full[slot], (it / NST) & 1, C.abort_flag)) {
+        if (!tc::mbar_wait(&C.full[slot], (it / NST) & 1, C.abort_flag, C.P.wait_ns)) {
             *(volatile int *)C.abort_flag = 1;
             break;
         }
@@ -506,13 +502,18 @@ __device__ __forceinline__ void role_mma(const Cta &C) {
         tc::mma_commit(&C.empty[slot]);
         if (it % SEG == SEG - 1 || it == C.nstg - 1) tc::mma_commit(&C.seg_full[b]);
     }
+    // every MMA this thread issued must have completed before the block frees
+    // the TMEM they write and the shared memory they read, also when the
+    // block gave up early (the drain's own limit, not the wait limit)
+    tc::mma_commit(C.drained);
+    tc::mbar_wait_plain(C.drained, 0, tc::kWaitLimitNs);
 }
 
 template <bool TF32, bool WRITE>
 __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     constexpr int SPS = Item<TF32>::SPS;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t full[NST], empty[NST], seg_full[2], seg_empty[2];
+    __shared__ uint64_t full[NST], empty[NST], seg_full[2], seg_empty[2], drained;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, sLast;
     __shared__ double red[THREADS / 32];
@@ -535,6 +536,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
             tc::mbar_init(&seg_full[i], 1);
             tc::mbar_init(&seg_empty[i], NDRAIN);
         }
+        tc::mbar_init(&drained, 1);
         abort_flag = 0;
         tc::fence_async_smem();
     }
@@ -545,7 +547,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const Cta C{P, smem, full, empty, seg_full, seg_empty, &abort_flag, tmem_base, t, k, pq.x, pq.y,
+    const Cta C{P, smem, full, empty, seg_full, seg_empty, &drained, &abort_flag, tmem_base, t, k, pq.x, pq.y,
                 nstg, (nstg + SEG - 1) / SEG, P.chan[k]};
     double chi = 0.0;
     if (warp < NDRAIN / 32) {
@@ -729,6 +731,7 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
     P.counter = c->d_scounter;
     P.result = result;
     P.status = c->d_status;
+    P.wait_ns = c->wait_ns ? c->wait_ns : tc::kWaitLimitNs;
     auto go = [&](auto kernel) -> cudaError_t {
         // the warpgroup register budgets assume the block is launched with
         // exactly REGS_LAUNCH registers per thread; never launch otherwise

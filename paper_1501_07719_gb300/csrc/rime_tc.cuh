@@ -85,16 +85,32 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Default limit of the bounded waits (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
 // Waits for the phase of the given parity to complete, sleeping in the
-// barrier between tests; gives up (returns false) when *abort is set by
-// another thread or after about two seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// barrier between tests (no longer than the limit); gives up (returns false)
+// when *abort is set by another thread or after lim_ns nanoseconds.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                          unsigned long long lim_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    const uint32_t hint = lim_ns < 20000ull ? (uint32_t)lim_ns : 20000u;
+    for (uint32_t i = 0; i < (1u << 30); i++) {
+        if (mbar_try_wait_sleep(bar, parity, hint)) return true;
+        if (*abort) return false;
+        if (global_ns() - t0 > lim_ns) return false;
+    }
+    return false;
+}
+// The same without an abort flag: for waits that must end before the block
+// frees what the awaited operations use (they give up only at the limit).
+__device__ __forceinline__ bool mbar_wait_plain(uint64_t *bar, uint32_t parity, unsigned long long lim_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t i = 0; i < (1u << 30); i++) {
         if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-        if (*abort) return false;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > lim_ns) return false;
     }
     return false;
 }

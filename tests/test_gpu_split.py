@@ -24,6 +24,13 @@ pytestmark = pytest.mark.gpu
 # cases.
 VTOL = {"bf16": 3e-5, "tf32": 3e-6}
 CTOL = {"bf16": 3e-4, "tf32": 5e-5}
+# The 256-antenna, 4096-source workload (|V| ~ 1e2 Jy, residuals at the noise
+# level), about 1.5 times the errors measured there: visibilities over
+# sampled (t, baseline, channel) BF16 3.9e-6, TF32 6.6e-7; chi^2 on timestep
+# 0, channels 0-1, BF16 7.1e-4, TF32 1.4e-5. BF16 does not reach the FP32
+# chi^2 bound of 1e-4 there; TF32 does.
+VTOL_256 = {"bf16": 6e-6, "tf32": 1e-6}
+CTOL_256 = {"bf16": 1.1e-3, "tf32": 2e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -157,8 +164,8 @@ def test_split_256ant_slice_chi2_against_oracle():
     # sources in FP32 and adds them into compensated running sums, and meets
     # the FP32 bound. The TF32 split adds short MMA segments into its running
     # sums too. The BF16 split's |dV| (~4e-6 of max |V|) shows at ~1e-3.
-    for mode, tol in ((R.RIME_TC_OFF, 1e-4), (R.RIME_TC_SPLIT_BF16, 2e-3),
-                      (R.RIME_TC_SPLIT_TF32, CTOL["tf32"])):
+    for mode, tol in ((R.RIME_TC_OFF, 1e-4), (R.RIME_TC_SPLIT_BF16, CTOL_256["bf16"]),
+                      (R.RIME_TC_SPLIT_TF32, CTOL_256["tf32"])):
         r.set_tensor_mode(mode)
         got = r.chi2()
         assert rel_err(got, want) <= tol, (mode, got, want)
@@ -190,4 +197,46 @@ def test_split_full_256ant_sampled(split):
     p, q = rime_synth.baseline_pairs(256)
     ref = oracle.Problem(inp).vis_list(t, p[bl], q[bl], k)
     err = np.abs(got - ref).max() / np.abs(ref).max()
-    assert err <= VTOL[split], err
+    assert err <= VTOL_256[split], err
+
+
+def test_phase_argument_matches_fp64_reduction():
+    """The phase argument of eq. 3 as the FP32 and split kernels form it
+    (double-float product, exact reduction) against the FP64 definition
+    nu tau - round(nu tau): within 2^-24 + 2^-47 |nu tau| turns over the
+    range the workloads reach (|nu tau| up to ~1e2 turns) and beyond."""
+    import paper_1501_07719_gb300 as R
+    rng = np.random.default_rng(11)
+    n = 200000
+    nu = rng.uniform(1.0e9, 1.5e9, n)
+    # delays |tau| <= 1e-6 s: |nu tau| up to 1.5e3 turns (the workloads: ~1e2)
+    tau = rng.uniform(-1e-6, 1e-6, n) * rng.choice([1e-3, 1e-2, 1e-1, 1.0], n)
+    got = R.rime_phase_turns(nu, tau).astype(np.float64)
+    want = oracle.reduced_phase(nu, tau)
+    # the same remainder (near +-1/2 either end is the same phase)
+    d = np.abs(got - want)
+    d = np.minimum(d, np.abs(d - 1.0))
+    bound = 2.0 ** -24 + 2.0 ** -47 * np.abs(nu * tau)
+    assert np.all(d <= bound), float((d / bound).max())
+
+
+@pytest.mark.parametrize("split", ["bf16", "tf32"])
+def test_bounded_wait_gives_up_and_the_next_call_recovers(split):
+    """With a 1 ns wait limit, the first wait of the tensor-core pipeline that
+    is not already satisfied gives up: the block records the timeout, waits
+    for the MMAs it issued, frees its tensor memory and returns, and the call
+    reports RIME_E_TIMEOUT. With the default limit the next call returns the
+    oracle's chi^2 (the tensor memory was freed, the status cleared)."""
+    import paper_1501_07719_gb300 as R
+    inp = make_case(**CASES["13ant-37src"], precision="f32")
+    want = oracle.Problem(inp, data=inp["data"]).chi2()
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(_mode(split))
+    r.set_wait_limit(1)
+    with pytest.raises(R.RimeError) as e:
+        r.chi2()
+    assert e.value.status == R._abi.RIME_E_TIMEOUT
+    r.set_wait_limit(0)
+    for _ in range(2):
+        assert rel_err(r.chi2(), want) <= CTOL[split]
+    r.close()

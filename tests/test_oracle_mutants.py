@@ -58,6 +58,8 @@ MUTANTS = [
     ("grad: gain q imaginary sign", "for (int c = 0; c < 4; c++) dVi[c] = -IMAG * dVr[c];",
      "for (int c = 0; c < 4; c++) dVi[c] = IMAG * dVr[c];"),
     ("grad: alpha derivative", "* log(lambda_ref / lambda);", "* log(lambda / lambda_ref);"),
+    ("reduced phase: floor for the nearest integer", "out[i] = x - nearbyint(x);", "out[i] = x - floor(x);"),
+    ("reduced phase: truncation", "out[i] = x - nearbyint(x);", "out[i] = x - trunc(x);"),
 ]
 
 

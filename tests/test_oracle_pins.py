@@ -526,3 +526,33 @@ def test_gradient_stokes_closed_form_linear():
         fd = (oracle.Problem(_set_param(inp, 1, j, x0 + h)).chi2()
               - oracle.Problem(_set_param(inp, 1, j, x0 - h)).chi2()) / (2 * h)
         assert gs[1, j] == pytest.approx(fd, rel=1e-9, abs=1e-12)
+
+
+def test_reduced_phase_exact_binary_fractions():
+    """nu tau - round(nu tau) for nu = 2^30 Hz and tau = (k + f) 2^-30 s, whose
+    product is exactly k + f: the remainder is f, with its sign, for large k
+    (rounding to the nearest integer, not down or toward zero)."""
+    nu = np.full(12, 2.0 ** 30)
+    k = np.array([0, 1, 17, 123456, -5, -77, 3, 9, 250, -250, 1000, 40])
+    f = np.array([0.25, -0.375, 0.125, 0.4375, -0.25, 0.375, -0.125, 0.0, 0.3125, -0.3125, 0.0625, -0.0625])
+    tau = (k + f) * 2.0 ** -30
+    np.testing.assert_array_equal(oracle.reduced_phase(nu, tau), f)
+
+
+def test_reduced_phase_range_ties_and_phase_factor():
+    """The remainder lies in [-1/2, 1/2] (halves go to the even integer), and
+    exp(2 pi i r) equals exp(2 pi i nu tau) (eq. 3's factor), checked with
+    Python's own cos and sin at moderate arguments."""
+    import math
+    nu = np.full(4, 2.0 ** 30)
+    tau = np.array([2.5, 3.5, -2.5, -3.5]) * 2.0 ** -30
+    np.testing.assert_array_equal(oracle.reduced_phase(nu, tau), [0.5, -0.5, -0.5, 0.5])
+    rng = np.random.default_rng(5)
+    nu = rng.uniform(1e9, 1.5e9, 200)
+    tau = rng.uniform(-1e-7, 1e-7, 200)
+    r = oracle.reduced_phase(nu, tau)
+    assert np.all(np.abs(r) <= 0.5)
+    for a, b, x in zip(nu, tau, r):
+        ph = 2 * math.pi * a * b
+        assert abs(math.cos(2 * math.pi * x) - math.cos(ph)) < 1e-12
+        assert abs(math.sin(2 * math.pi * x) - math.sin(ph)) < 1e-12
