@@ -42,12 +42,16 @@ def peak_fp32_tflops(mhz):
     return 2.0 * FP32_LANES_PER_SM * SM_COUNT * mhz * 1e6 / 1e12
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "fused_chi2_fp32_64ant.traffic.txt")
+
+
 def profiled_traffic():
     """DRAM bytes per launch of the fused chi^2 kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+    record (key: value lines), or None when the kernel source changed since
+    the capture."""
     import hashlib
     try:
-        text = open(os.path.join(ROOT, "profiles", "fused_chi2_fp32_64ant.md")).read()
+        text = open(TRAFFIC_RECORD).read()
         src = open(os.path.join(ROOT, "paper_1501_07719_gb300", "csrc", "rime_fused.cu"), "rb").read()
     except OSError:
         return None
@@ -479,6 +483,38 @@ def form_sweep(torch, R):
                     "Table 4 (full RIME + chi^2 on a K40), context not target"}
 
 
+def form_peaks(torch, R):
+    """Measured issue rates of the FP32 (scalar and packed), FP64 and SFU
+    pipes (rime_pipe_rate), with the SM clock sampled while they run: the
+    denominators of the ALU rooflines."""
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.2)
+    rates = {name: R.rime_pipe_rate(pipe) for name, pipe in
+             (("ffma", R.RIME_PIPE_FFMA), ("ffma2", R.RIME_PIPE_FFMA2), ("dfma", R.RIME_PIPE_DFMA),
+              ("ex2", R.RIME_PIPE_EX2))}
+    clocks = clk.stop()
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    per_clk = {k: v / (SM_COUNT * mhz * 1e6) for k, v in rates.items()}
+    return {"lane_ops_per_s": rates, "per_sm_per_clock": per_clk, "clocks": clocks,
+            "note": "one FMA counts one lane operation (a packed pair two); flops = 2 x FMA rate"}
+
+
+def form_fp64(torch, R):
+    """The FP64 fused chi^2 of the benchmark workload: time, terms/s and its
+    roofline against the measured FP64 FMA rate."""
+    wl = rime_synth.WORKLOADS[WORKLOAD]
+    ms = _sweep_time(torch, R, wl, True, 3)
+    dfma = R.rime_pipe_rate(R.RIME_PIPE_DFMA)
+    peak = 2.0 * dfma / 1e12
+    ach = algo_flops(wl) / (ms * 1e-3) / 1e12
+    return {"workload": wl.name, "dtype": "f64", "ms": ms, "terms_per_s": terms_of(wl) / (ms * 1e-3),
+            "roofline": {"bound": "alu", "kernel": "k_fused_f64<chi2>", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak,
+                         "peak_basis": "measured FP64 FMA rate (rime_pipe_rate) x 2 flops",
+                         "algorithmic": f"{FLOPS_POINT} flops/point term, {FLOPS_GAUSS}/Gaussian term"}}
+
+
 def run_only(args):
     """One form on one (possibly reduced) workload, for profiling: prints the
     median launch time. Not the benchmark line."""
@@ -539,18 +575,24 @@ def run_reference(args, wl, rank, world):
     import oracle
     inp = rime_synth.make_inputs(wl, precision="f32")
     nt, nch = oracle.threads(), 8
-    vals, cb = [], None
+    vals, secs, cb = [], [], None
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         cb = cpu_baseline(wl, inp, nt, nch)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
             vals.append(cb["value"])
+            secs.append(dt)
     value = statistics.median(vals) if vals else cb["value"]
     cb["value"] = value
+    # one step is one oracle chi^2 of the sample: its own time, not the full workload's
+    ms_step = 1e3 * (statistics.mean(secs) if secs else 0.0)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "terms/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": terms_of(wl) / value * 1e3, "higher_is_better": True,
+            "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "precision": "f64 oracle", "sample": cb["sample"]},
+            "config": {"workload": wl.name, "precision": "f64 oracle", "sample": cb["sample"],
+                       "step": "one oracle chi^2 of the sample (the value is the sample's terms / its time)"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -569,16 +611,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the gradient, batched and split-precision comparisons")
-    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep", "chains"],
+    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep", "chains",
+                                       "peaks", "fp64"],
                     help="time one form on --workload (optionally with fewer timesteps / channels) "
                          "instead of the benchmark; for profiling")
     ap.add_argument("--ntime", type=int, default=0)
     ap.add_argument("--nchan", type=int, default=0)
     args = ap.parse_args()
-    if args.only == "sweep":
+    if args.only in ("sweep", "peaks", "fp64"):
         import torch
         import paper_1501_07719_gb300 as R
-        print(json.dumps(form_sweep(torch, R)), flush=True)
+        fn = {"sweep": form_sweep, "peaks": form_peaks, "fp64": form_fp64}[args.only]
+        print(json.dumps(fn(torch, R)), flush=True)
         return 0
     if args.only:
         return run_only(args)
@@ -701,7 +745,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_fused<float, chi2>", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic() if args.workload == WORKLOAD else None,
-                     "traffic_unit": "bytes per launch (ncu dram read + write, profiles/fused_chi2_fp32_64ant.md)",
+                     "traffic_unit": "bytes per launch (ncu dram read + write, " + os.path.relpath(TRAFFIC_RECORD, ROOT) + ")",
                      "peak_basis": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz",
                      "algorithmic": f"{FLOPS_POINT} flops/point term, {FLOPS_GAUSS}/Gaussian term",
                      "avg_launch_ms": avg_launch_s * 1e3},
@@ -720,7 +764,9 @@ def main():
         line["roofline"]["frac_at_median_clock"] = achieved / peak_fp32_tflops(clocks["sm_mhz"])
     ctx.close()
     if rank == 0 and world == 1 and not args.no_forms and args.precision == "f32":
-        line["forms"] = {"small_fp64_latency": form_small_latency(torch, R),
+        line["forms"] = {"peaks": form_peaks(torch, R),
+                         "fp64": form_fp64(torch, R),
+                         "small_fp64_latency": form_small_latency(torch, R),
                          "gradient": form_grad(torch, R, ms_per_step),
                          "batched": form_batched(torch, R),
                          "sampler": form_sampler(torch, R),

@@ -426,6 +426,24 @@ rime_status rime_chi2_noalloc(const rime_dims *dims, const double *freq_hz, cons
  * from rime_last_error(NULL)). */
 rime_status rime_phase_turns(int64_t n, const double *nu_hz, const double *tau_s, float *turns);
 
+/* Arithmetic pipes whose issue rates the roofline fractions of this
+ * library's kernels are quoted against (rime_pipe_rate). The paper has no
+ * counterpart to this call: it quotes its K40's nominal peaks (Sec. 4.3). */
+typedef enum {
+    RIME_PIPE_FFMA = 0,   /* FP32 fused multiply-add */
+    RIME_PIPE_FFMA2 = 1,  /* FP32 FMA on packed pairs (counted as two) */
+    RIME_PIPE_DFMA = 2,   /* FP64 fused multiply-add */
+    RIME_PIPE_EX2 = 3     /* the SFU's exp2 approximation */
+} rime_pipe;
+
+/* Measures the rate of one pipe on the current device with a kernel of
+ * independent register-resident chains over every SM (about 20 ms per
+ * launch; uses the legacy default stream and a small temporary buffer).
+ *   pipe        a rime_pipe
+ *   ops_per_s   out: lane operations per second (one FMA counts one)
+ * Errors: RIME_E_INVALID, RIME_E_OOM, RIME_E_CUDA. */
+rime_status rime_pipe_rate(int32_t pipe, double *ops_per_s);
+
 /* The message for the last failed call on this context ("" if none). */
 const char *rime_last_error(const rime_ctx *ctx);
 

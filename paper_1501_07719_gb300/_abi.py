@@ -19,6 +19,7 @@ RIME_FP32, RIME_FP64 = 0, 1
 RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 = 0, 1, 2
 RIME_KERNEL_AUTO, RIME_KERNEL_TILED, RIME_KERNEL_NARROW = 0, 1, 2
 RIME_BEAM_COS3, RIME_BEAM_JINC = 0, 1
+RIME_PIPE_FFMA, RIME_PIPE_FFMA2, RIME_PIPE_DFMA, RIME_PIPE_EX2 = 0, 1, 2, 3
 
 
 class rime_dims(C.Structure):
@@ -86,6 +87,7 @@ def lib():
         L.rime_chi2_streamed.argtypes = [vp, vp, vp, C.c_int32, C.POINTER(C.c_double)]
         L.rime_stream_chunk_ntime.argtypes, L.rime_stream_chunk_ntime.restype = [vp], C.c_int32
         L.rime_phase_turns.argtypes, L.rime_phase_turns.restype = [C.c_int64, vp, vp, vp], ip
+        L.rime_pipe_rate.argtypes, L.rime_pipe_rate.restype = [C.c_int32, C.POINTER(C.c_double)], ip
         for f in ("rime_chi2_batched", "rime_batched_config", "rime_set_batched_config", "rime_set_tensor_mode",
                   "rime_set_kernel", "rime_chi2_streamed", "rime_set_beam", "rime_chains_init",
                   "rime_chains_propose", "rime_chains_accept"):
@@ -379,3 +381,10 @@ def rime_phase_turns(nu_hz, tau_s) -> np.ndarray:
 def rime_set_wait_limit(ctx, ns: int):
     """Limit (ns) of the tensor-core kernels' bounded waits; 0: the default (about 2 s)."""
     _check(lib().rime_set_wait_limit(ctx, int(ns)), ctx)
+
+
+def rime_pipe_rate(pipe: int) -> float:
+    """Measured lane operations per second of one arithmetic pipe (RIME_PIPE_*)."""
+    out = C.c_double()
+    _check(lib().rime_pipe_rate(int(pipe), C.byref(out)), None)
+    return out.value

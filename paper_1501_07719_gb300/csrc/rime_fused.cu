@@ -289,7 +289,7 @@ namespace f32 {
 #define RIME_F32_MIN_BLOCKS 2   // resident blocks per SM the register budget is sized for
 #endif
 #ifndef RIME_F32_SC
-#define RIME_F32_SC 20          // sources per staged chunk
+#define RIME_F32_SC 32          // sources per staged chunk
 #endif
 constexpr int THREADS = 256;
 constexpr int SC = RIME_F32_SC;      // sources per chunk
@@ -316,22 +316,21 @@ __device__ __forceinline__ int apad(int a) { return a + ((a >> 3) << 2); }
 // tiles that load more per FMA (a 1 x 8 tile needs eight loads).
 //
 // The Gaussian exponent of baseline (p, q) for source s is the quadratic form
-// Qf(x_p - x_q) of the antenna coordinates x = (u, v); it is evaluated as
-// Qf(x_p) + Qf(x_q) - x_p . L(x_q) with L(x) = grad Qf(x), from per-antenna
-// values staged with the factors. A chunk of point sources runs a loop
-// without shape factors.
+// e = A du^2 + B du dv + C dv^2 of the baseline (du, dv) = x_p - x_q: the
+// three products of each baseline are formed once per work item and held in
+// registers, and A, B, C (times nu^2) come with the source. A chunk of point
+// sources runs a loop without shape factors.
 struct Smem {
     float Kx[SC * RSTR], Ky[SC * RSTR];            // staged A = x + iy, row antennas
     float Cx[SC * CSTR], Cy[SC * CSTR];            // column antennas (off-diagonal units)
-    float Qr[SC * RSTR], Lxr[SC * RSTR], Lyr[SC * RSTR];   // Gaussian form, row antennas
-    float Qc[SC * CSTR], Lxc[SC * CSTR], Lyc[SC * CSTR];   // Gaussian form, columns
     float2 rTau[SC * NLOC];     // prefetched delays (hi, lo) of the next chunk
     float rRho[SC * NLOC];      // prefetched beam radii
     float4 rSt[SC];             // prefetched Stokes
     float4 rG[SC];              // prefetched Gaussian coefficients
     float rAl[SC];              // prefetched spectral indices
     float4 St[SC];              // (I, Q, U, V) scaled (see staging)
-    float Gf[SC];               // source kind: 0 point, 1 Gaussian, 2 exponential disk
+    float4 Gq[SC];              // shape form (A, B, C) nu^2 of the baseline (du, dv); w: kind
+                                // (0 point, 1 Gaussian, 2 exponential disk)
     float2 uv[NLOC];            // antenna (u, v) at this timestep, unit order
     float GG[NLOC * 8];         // gradient mode: per-antenna gains gradient of this block
     double red[32];
@@ -382,13 +381,16 @@ __device__ __forceinline__ void accumulate2(Pair &acc, float2 ax, float2 ay, flo
         acc.im[c] = __ffma2_rn(zi, X[c], acc.im[c]);
     }
 }
-// Shape factors of two slots from the quadratic form e = Qf(x_p) + Qf(x_q) -
-// x_p . L(x_q) of the baseline: Gaussian 2^e (log2 units), exponential disk
+// Shape factors of two slots from the quadratic form of their baselines,
+// e = A du^2 + B du dv + C dv^2: Gaussian 2^e (log2 units), exponential disk
 // (1 + e)^(-3/2) (only in the kernels built for general sky models).
+struct Geo {
+    float2 d2[4], dd[4], v2[4];   // (du^2, du dv, dv^2) of the slot pairs
+};
 template <bool GENERAL>
-__device__ __forceinline__ float2 shape2(bool disk, float2 qp, float2 up, float2 vp, float2 qq, float2 lx, float2 ly) {
-    const float2 e = __ffma2_rn(f2(-up.x, -up.y), lx, __ffma2_rn(f2(-vp.x, -vp.y), ly, __fadd2_rn(qp, qq)));
-    if (GENERAL && disk) {
+__device__ __forceinline__ float2 shape2(const float4 &q, const Geo &G, int h) {
+    const float2 e = __ffma2_rn(f2(q.x, q.x), G.d2[h], __ffma2_rn(f2(q.y, q.y), G.dd[h], __fmul2_rn(f2(q.z, q.z), G.v2[h])));
+    if (GENERAL && q.w > 1.5f) {
         const float r0 = rsqrtf(1.0f + e.x), r1 = rsqrtf(1.0f + e.y);
         return f2(r0 * r0 * r0, r1 * r1 * r1);
     }
@@ -397,20 +399,10 @@ __device__ __forceinline__ float2 shape2(bool disk, float2 qp, float2 up, float2
 
 // One chunk of sources for a 2 x 4 body tile (rows at ip, columns at iq of
 // the staged rows; cstr the column rows' stride).
-#ifndef RIME_F32_UNROLL_PT
-#define RIME_F32_UNROLL_PT 1    // unrolling of the body tiles' point-source loop
-#endif
-#ifndef RIME_F32_UNROLL_EXT
-#define RIME_F32_UNROLL_EXT 1   // ... and of their loop with shape factors
-#endif
-#define RIME_PRAGMA(x) _Pragma(#x)
-#define RIME_UNROLL(n) RIME_PRAGMA(unroll n)
 template <bool SHAPE, bool GENERAL>
 __device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const float *KxC, const float *KyC,
-                                           const float *QC, const float *LxC, const float *LyC, int cstr, int ip,
-                                           int iq, int sc, float2 (&up)[2], float2 (&vp)[2]) {
-    constexpr int UNR = SHAPE ? RIME_F32_UNROLL_EXT : RIME_F32_UNROLL_PT;
-    RIME_UNROLL(UNR)
+                                           int cstr, int ip, int iq, int sc, const Geo &G) {
+#pragma unroll 1
     for (int s = 0; s < sc; s++) {
         const float2 kr = *reinterpret_cast<const float2 *>(S.Kx + s * RSTR + ip);
         const float2 ki = *reinterpret_cast<const float2 *>(S.Ky + s * RSTR + ip);
@@ -419,27 +411,14 @@ __device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S
         const float4 x = S.St[s];
         const float2 X[4] = {f2(x.x, x.x), f2(x.y, x.y), f2(x.z, x.z), f2(x.w, x.w)};
         const float2 bx[2] = {f2(bx4.x, bx4.y), f2(bx4.z, bx4.w)}, by[2] = {f2(by4.x, by4.y), f2(by4.z, by4.w)};
-        float2 g[4] = {f2(1.f, 1.f), f2(1.f, 1.f), f2(1.f, 1.f), f2(1.f, 1.f)};
-        if (SHAPE) {
-            const bool disk = S.Gf[s] > 1.5f;
-            const float2 qr = *reinterpret_cast<const float2 *>(S.Qr + s * RSTR + ip);
-            const float4 q4 = *reinterpret_cast<const float4 *>(QC + s * cstr + iq);
-            const float4 lx4 = *reinterpret_cast<const float4 *>(LxC + s * cstr + iq);
-            const float4 ly4 = *reinterpret_cast<const float4 *>(LyC + s * cstr + iq);
-            const float2 qq[2] = {f2(q4.x, q4.y), f2(q4.z, q4.w)};
-            const float2 lx[2] = {f2(lx4.x, lx4.y), f2(lx4.z, lx4.w)}, ly[2] = {f2(ly4.x, ly4.y), f2(ly4.z, ly4.w)};
-#pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const int r = h >> 1, c = h & 1;
-                const float qpr = r ? qr.y : qr.x;
-                g[h] = shape2<GENERAL>(disk, f2(qpr, qpr), up[r], vp[r], qq[c], lx[c], ly[c]);
-            }
-        }
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SHAPE) q = S.Gq[s];
 #pragma unroll
         for (int h = 0; h < 4; h++) {
             const int r = h >> 1, c = h & 1;
             const float xr = r ? kr.y : kr.x, yr = r ? ki.y : ki.x;
-            accumulate2<SHAPE>(acc[h], f2(xr, xr), f2(yr, yr), bx[c], by[c], g[h], X);
+            const float2 g = SHAPE ? shape2<GENERAL>(q, G, h) : f2(1.f, 1.f);
+            accumulate2<SHAPE>(acc[h], f2(xr, xr), f2(yr, yr), bx[c], by[c], g, X);
         }
     }
 }
@@ -447,7 +426,7 @@ __device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S
 // One chunk for a head tile: pairs inside one 8-antenna block, rows x_0 and x_4.
 template <bool SHAPE, bool GENERAL>
 __device__ __forceinline__ void head_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const Tile &tl, int sc,
-                                           float2 (&up)[2], float2 (&vp)[2]) {
+                                           const Geo &G) {
     const int hb = apad(tl.p), r = tl.fold;
     int ho[8];   // shared-memory offsets of x_0..x_7 (one 8-antenna block)
 #pragma unroll
@@ -459,19 +438,14 @@ __device__ __forceinline__ void head_chunk(Pair (&acc)[NSLOT / 2], const Smem &S
         const float *kx = S.Kx + s * RSTR, *ky = S.Ky + s * RSTR;
         const float2 ax[2] = {f2(kx[ho[0]], kx[ho[0]]), f2(kx[ho[4]], kx[ho[4]])};
         const float2 ay[2] = {f2(ky[ho[0]], ky[ho[0]]), f2(ky[ho[4]], ky[ho[4]])};
-        const bool disk = S.Gf[s] > 1.5f;
-        const float *qq = S.Qr + s * RSTR, *lx = S.Lxr + s * RSTR, *ly = S.Lyr + s * RSTR;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SHAPE) q = S.Gq[s];
 #pragma unroll
         for (int h = 0; h < 4; h++) {
             const int r2 = h < 2 ? 0 : 1;
             const int c0 = ho[2 * h + 1], c1 = h < 3 ? ho[2 * h + 2] : ho[0];   // slot 7 unused
             const float2 bx = f2(kx[c0], kx[c1]), by = f2(ky[c0], ky[c1]);
-            float2 g = f2(1.f, 1.f);
-            if (SHAPE) {
-                const float qps = qq[ho[4 * r2]];
-                g = shape2<GENERAL>(disk, f2(qps, qps), up[r2], vp[r2], f2(qq[c0], qq[c1]), f2(lx[c0], lx[c1]),
-                                    f2(ly[c0], ly[c1]));
-            }
+            const float2 g = SHAPE ? shape2<GENERAL>(q, G, h) : f2(1.f, 1.f);
             accumulate2<SHAPE>(acc[h], ax[r2], ay[r2], bx, by, g, X);
         }
     }
@@ -593,9 +567,6 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     }
     const float *KxC = U.diag ? S.Kx : S.Cx;
     const float *KyC = U.diag ? S.Ky : S.Cy;
-    const float *QC = U.diag ? S.Qr : S.Qc;
-    const float *LxC = U.diag ? S.Lxr : S.Lxc;
-    const float *LyC = U.diag ? S.Lyr : S.Lyc;
     const int cstr = U.diag ? RSTR : CSTR;
     const bool pointing = P.has_pointing != 0;
 
@@ -604,8 +575,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     for (int h = 0; h < NSLOT / 2; h++)
 #pragma unroll
         for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
-    // the rows' antenna coordinates, as pairs (filled after the first barrier)
-    float2 up[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, vp[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+    Geo geo;   // the baselines' (du^2, du dv, dv^2), filled after the first barrier
     int nacc = 0;        // sources in the current register segment (long lists)
     bool held = false;   // earlier segments are in the running sums
 
@@ -624,18 +594,12 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 v.x *= E;
                 v.y *= E;
             }
-            const float4 g = S.rG[s];
-            const float2 xa = S.uv[a];
-            // Gaussian form (log2 units, times nu^2): Qf(x), grad Qf(x)
-            const float A = g.x * ch.nu2, B = g.y * ch.nu2, C = g.z * ch.nu2;
-            const float q = xa.x * fmaf(A, xa.x, B * xa.y) + C * xa.y * xa.y;
-            const float lx = fmaf(2.f * A, xa.x, B * xa.y), ly = fmaf(B, xa.x, 2.f * C * xa.y);
             if (a < U.nr) {
                 const int o = s * RSTR + apad(a);
-                S.Kx[o] = v.x; S.Ky[o] = v.y; S.Qr[o] = q; S.Lxr[o] = lx; S.Lyr[o] = ly;
+                S.Kx[o] = v.x; S.Ky[o] = v.y;
             } else {
                 const int o = s * CSTR + apad(a - U.nr);
-                S.Cx[o] = v.x; S.Cy[o] = v.y; S.Qc[o] = q; S.Lxc[o] = lx; S.Lyc[o] = ly;
+                S.Cx[o] = v.x; S.Cy[o] = v.y;
             }
             a += it_da;
             s += it_ds;
@@ -651,30 +615,46 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             }
             float4 st = S.rSt[tid];
             S.St[tid] = make_float4(st.x * f, st.y * f, st.z * f, st.w * f);
-            S.Gf[tid] = S.rG[tid].w;
-            ext = S.rG[tid].w != 0.f;
+            const float4 g = S.rG[tid];
+            // the shape form in log2 units times nu^2 (Gaussians), or times nu^2
+            // with the disk's constant (disks)
+            S.Gq[tid] = make_float4(g.x * ch.nu2, g.y * ch.nu2, g.z * ch.nu2, g.w);
+            ext = g.w != 0.f;
         }
         // the chunk has an extended source if any thread saw one
         ext = __syncthreads_or(ext) != 0;
         if (s0 + SC < se) issue(s0 + SC);
         if (s0 == sb) {
+            // (du^2, du dv, dv^2) of each slot's baseline, in slot pairs
+            float d2[NSLOT], dd[NSLOT], v2[NSLOT];
 #pragma unroll
-            for (int r = 0; r < 2; r++) {
-                const int a = role == 2 ? tl.p + ((tl.fold + 4 * r) & 7) : min(tl.p + r, nloc - 1);
-                const float2 x = S.uv[role == 0 ? 0 : a];
-                up[r] = f2(x.x, x.x);
-                vp[r] = f2(x.y, x.y);
+            for (int j = 0; j < NSLOT; j++) {
+                int pj, qj;
+                bool rev;
+                slot_pair(tl, role, j, pj, qj, rev);
+                const bool ok = (mask >> j) & 1u;
+                const float2 a = S.uv[ok ? pj : 0], b = S.uv[ok ? (U.diag ? qj : U.nr + qj) : 0];
+                const float du = a.x - b.x, dv = a.y - b.y;
+                d2[j] = du * du;
+                dd[j] = du * dv;
+                v2[j] = dv * dv;
+            }
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                geo.d2[h] = f2(d2[2 * h], d2[2 * h + 1]);
+                geo.dd[h] = f2(dd[2 * h], dd[2 * h + 1]);
+                geo.v2[h] = f2(v2[2 * h], v2[2 * h + 1]);
             }
         }
 
         // ---- source sum for this thread's baselines (Algorithm 2) ----
         if (role == 1) {
             const int ip = apad(tl.p), iq = apad(tl.q);
-            if (ext) body_chunk<true, GENERAL>(acc, S, KxC, KyC, QC, LxC, LyC, cstr, ip, iq, sc, up, vp);
-            else body_chunk<false, GENERAL>(acc, S, KxC, KyC, QC, LxC, LyC, cstr, ip, iq, sc, up, vp);
+            if (ext) body_chunk<true, GENERAL>(acc, S, KxC, KyC, cstr, ip, iq, sc, geo);
+            else body_chunk<false, GENERAL>(acc, S, KxC, KyC, cstr, ip, iq, sc, geo);
         } else if (role == 2) {
-            if (ext) head_chunk<true, GENERAL>(acc, S, tl, sc, up, vp);
-            else head_chunk<false, GENERAL>(acc, S, tl, sc, up, vp);
+            if (ext) head_chunk<true, GENERAL>(acc, S, tl, sc, geo);
+            else head_chunk<false, GENERAL>(acc, S, tl, sc, geo);
         }
         if constexpr (SEGD) {
             nacc += sc;
