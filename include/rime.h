@@ -167,10 +167,11 @@ rime_status rime_chi2_async(rime_ctx *ctx, double *chi2_dev);
  *               gradient d chi^2/dRe G + i d chi^2/dIm G of each Jones entry
  *               (with identity gains when none are set)
  * Needs static brightness (time_varying = 0), else RIME_E_INVALID. Uses a
- * device buffer of one complex Y_X per visibility and correlation and one
- * partial per (t, channel, antenna unit, source), allocated on first use.
- * The gains gradient is summed with floating-point atomics (not bit-for-bit
- * reproducible across runs); the source gradient is summed in a fixed order. */
+ * device buffer of one complex Y_X per visibility and correlation, one
+ * partial per (t, channel, antenna unit, source) and, when grad_gains is
+ * given, the 8 complex gains-gradient terms of each visibility (16 values of
+ * the context's precision), all allocated on first use. Every sum runs in a
+ * fixed order: repeated calls give bit-identical results. */
 rime_status rime_chi2_grad(rime_ctx *ctx, double *chi2, double *grad_src, void *grad_gains);
 
 /* sum over visibilities of ln(2 pi / w) (the second term of eq. 7), so that

@@ -66,7 +66,8 @@ void free_all(rime_ctx *c) {
                     c->d_tiles, c->d_partials, c->d_counter, c->d_status, c->d_yadj, c->d_gpart,
                     c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
                     c->d_spart, c->d_scounter, c->d_sscale, c->d_schi,
-                    c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part, c->d_segsum};
+                    c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part, c->d_segsum,
+                    c->d_dgain};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : c->d_sbuf)
@@ -492,14 +493,17 @@ rime_status rime_chi2_grad(rime_ctx *c, double *chi2, double *grad_src, void *gr
     Alloc alloc{c};
     if (!c->d_yadj) CK(c, alloc(&c->d_yadj, vis_count(c) * 4 * 2 * c->tsize()), "allocating the adjoint buffer");
     double *gg = static_cast<double *>(grad_gains);
-    if (gg)
-        CK(c, cudaMemsetAsync(gg, 0, (size_t)c->dims.ntime * c->dims.na * c->dims.nchan * 8 * sizeof(double),
-                              c->stream), "clearing grad_gains");
+    // the gains gradient: the forward kernel stores each visibility's two
+    // terms, a second kernel sums them per antenna in a fixed order
+    if (gg && !c->d_dgain)
+        CK(c, alloc(&c->d_dgain, vis_count(c) * 16 * c->tsize()), "allocating the gains-gradient terms");
+    void *dg = gg ? c->d_dgain : nullptr;
     if (narrow_applies(c))
-        CK(c, launch_narrow(c, MODE_GRAD, nullptr, &c->d_status->chi2, 0, c->nsrc, c->d_yadj, gg),
+        CK(c, launch_narrow(c, MODE_GRAD, nullptr, &c->d_status->chi2, 0, c->nsrc, c->d_yadj, dg),
            "gradient forward kernel");
     else
-        CK(c, launch_fused_mode(c, MODE_GRAD, nullptr, &c->d_status->chi2, c->d_yadj, gg), "gradient forward kernel");
+        CK(c, launch_fused_mode(c, MODE_GRAD, nullptr, &c->d_status->chi2, c->d_yadj, dg), "gradient forward kernel");
+    if (gg) CK(c, launch_gains_grad(c, gg), "gains gradient kernel");
     CK(c, launch_grad_src(c, grad_src), "source gradient kernels");
     rime_status s = sync_status(c);
     if (s != RIME_OK) return s;

@@ -59,6 +59,7 @@ constexpr int kGsets[] = {1, 4, 16};
 
 struct Sched {
     int nsets;
+    int max_set;          // sources of the largest set
     int per_set;          // partials per set
     const int *order[2];  // device: by size, by index
     const int *offsets;   // device
@@ -77,6 +78,7 @@ BatchParams batch_params(rime_ctx *c, const Sched &S, const rime_batch_config &c
     B.offsets = S.offsets;
     B.counter = c->d_bcounter;
     B.partials = c->d_bpart;
+    B.max_set = S.max_set;
     return B;
 }
 
@@ -213,7 +215,8 @@ rime_status rime_chi2_batched(rime_ctx *c, int32_t nsets, const int32_t *off, co
     CKB(c, put_ints(c->d_bsched + cap, host.data() + cap, nsets, c->stream), "uploading the schedule");
     CKB(c, put_ints(c->d_bsched + 2 * cap, host.data() + 2 * cap, (size_t)nsets + 1, c->stream),
         "uploading the schedule");
-    Sched S{nsets, (int)per_set, {c->d_bsched, c->d_bsched + cap}, c->d_bsched + 2 * cap};
+    const int max_set = off[host[0] + 1] - off[host[0]];   // host[0]: the largest set's index
+    Sched S{nsets, max_set, (int)per_set, {c->d_bsched, c->d_bsched + cap}, c->d_bsched + 2 * cap};
 
     if (c->bmax_bps == 0) {
         c->bmax_bps = std::max(1, batched_blocks_per_sm());

@@ -64,8 +64,7 @@ constexpr int ASTRIDE = ROWS + 4;
 struct D4 { double x, y, z, w; };
 constexpr int NLOCMAX = ROWS + COLS;
 constexpr size_t smem_bytes() {
-    return 2 * SC * ASTRIDE * sizeof(double2) + 2 * SC * sizeof(D4) + 64 * sizeof(double) +
-           NLOCMAX * 8 * sizeof(double);
+    return 2 * SC * ASTRIDE * sizeof(double2) + 2 * SC * sizeof(D4) + 64 * sizeof(double);
 }
 
 __device__ __forceinline__ double2 antenna_factor(double tau, double rho, double alpha, const ChanD &ch) {
@@ -86,7 +85,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     D4 *sSt = reinterpret_cast<D4 *>(sA + 2 * SC * ASTRIDE);         // [SC]
     D4 *sGq = sSt + SC;                                              // [SC]
     double *sRed = reinterpret_cast<double *>(sGq + SC);             // [64]
-    double *sGG = sRed + 64;                                         // [NLOCMAX][8] gains gradient
     __shared__ int sLast;
 
     if (inputs_bad(P.status)) return;
@@ -205,10 +203,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
     const double2 *data = reinterpret_cast<const double2 *>(P.data);
     const double *weight = reinterpret_cast<const double *>(P.weight);
     double2 *vis = reinterpret_cast<double2 *>(P.vis_out);
-    if constexpr (GRAD) {
-        for (int i = tid; i < NLOCMAX * 8; i += THREADS) sGG[i] = 0.0;
-        __syncthreads();
-    }
     const double2 I2[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
 #pragma unroll
     for (int i = 0; i < TP; i++)
@@ -254,26 +248,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_fused_f64(const FusedParams P) {
                     double2 *yo = reinterpret_cast<double2 *>(P.yout) + 4 * row;
 #pragma unroll
                     for (int c = 0; c < 4; c++) yo[c] = Y[c];
-                    const int lp = p - U.r0, lq = U.diag ? q - U.r0 : U.nr + (q - U.c0);
-                    if (P.grad_gains)
+                    if (P.dgain) {   // this visibility's terms of the gains gradient
+                        double2 *go = reinterpret_cast<double2 *>(P.dgain) + 4 * row;
+                        const long long plane = 4ll * P.ntime * P.nbl * P.nchan;
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        atomicAdd(&sGG[lp * 8 + 2 * c], dGp[c].x);
-                        atomicAdd(&sGG[lp * 8 + 2 * c + 1], dGp[c].y);
-                        atomicAdd(&sGG[lq * 8 + 2 * c], dGq[c].x);
-                        atomicAdd(&sGG[lq * 8 + 2 * c + 1], dGq[c].y);
+                        for (int c = 0; c < 4; c++) {
+                            go[c] = dGp[c];
+                            go[plane + c] = dGq[c];
+                        }
                     }
                 }
             }
         }
-    if constexpr (GRAD) {
-        __syncthreads();
-        for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
-            const int a = i >> 3;
-            const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
-            atomicAdd(&P.grad_gains[8 * (((long long)t * P.na + ant) * P.nchan + k) + (i & 7)], sGG[i]);
-        }
-    }
     if constexpr (CHI2) {
         double bsum = block_sum<THREADS>(chi, sRed);
         finish_chi2<THREADS>(bsum, P, sRed, &sLast);
@@ -332,7 +318,6 @@ struct Smem {
     float4 Gq[SC];              // shape form (A, B, C) nu^2 of the baseline (du, dv); w: kind
                                 // (0 point, 1 Gaussian, 2 exponential disk)
     float2 uv[NLOC];            // antenna (u, v) at this timestep, unit order
-    float GG[NLOC * 8];         // gradient mode: per-antenna gains gradient of this block
     double red[32];
 };
 
@@ -469,6 +454,12 @@ constexpr int SEG = 240;
 __device__ __forceinline__ float *seg_base(const FusedParams &P) {
     return P.segsum + (size_t)blockIdx.x * 2 * 64 * THREADS + threadIdx.x;
 }
+__device__ __forceinline__ void zero_sums(Pair (&acc)[NSLOT / 2]) {
+#pragma unroll
+    for (int h = 0; h < NSLOT / 2; h++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
+}
 template <typename F>
 __device__ __forceinline__ void each_sum(Pair (&acc)[NSLOT / 2], F &&f) {
 #pragma unroll
@@ -501,8 +492,13 @@ __device__ __forceinline__ void unfold_segments(const FusedParams &P, Pair (&acc
     each_sum(acc, [&](int f, float &v) { v = hi[f * THREADS] + (lo[f * THREADS] + v); });
 }
 
-template <int MODE, bool GENERAL, bool SEGD = false>
-__device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se) {
+// SUM: the source sum of [sb, se) is added into acc (the caller zeroes it);
+// EPI: the epilogue of the item from acc (sb, se unused). The kernel of one
+// launch per item runs both in one body (lists of up to 2 SEG sources); the
+// persistent kernels sum through source_sum and then run the epilogue.
+template <int MODE, bool GENERAL, bool SUM, bool EPI>
+__device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se,
+                                             Pair (&acc)[NSLOT / 2]) {
     constexpr bool CHI2 = MODE != MODE_PREDICT, WRITE = MODE == MODE_PREDICT, GRAD = MODE == MODE_GRAD;
     const int tid = threadIdx.x;
     const Unit U = P.units[u];
@@ -536,11 +532,13 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
         }
         cp_async_commit();
     };
-    if (se > sb) issue(sb);
-    for (int a = tid; a < nloc; a += THREADS) {
-        int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
-        float4 x = P.uvw_f[(long long)t * P.na + ant];
-        S.uv[a] = f2(x.x, x.y);
+    if constexpr (SUM) {
+        if (se > sb) issue(sb);
+        for (int a = tid; a < nloc; a += THREADS) {
+            int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
+            float4 x = P.uvw_f[(long long)t * P.na + ant];
+            S.uv[a] = f2(x.x, x.y);
+        }
     }
 
     // ---- this thread's 8 baselines ----
@@ -570,16 +568,9 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     const int cstr = U.diag ? RSTR : CSTR;
     const bool pointing = P.has_pointing != 0;
 
-    Pair acc[NSLOT / 2];
-#pragma unroll
-    for (int h = 0; h < NSLOT / 2; h++)
-#pragma unroll
-        for (int c = 0; c < 4; c++) acc[h].re[c] = acc[h].im[c] = f2(0.f, 0.f);
     Geo geo;   // the baselines' (du^2, du dv, dv^2), filled after the first barrier
-    int nacc = 0;        // sources in the current register segment (long lists)
-    bool held = false;   // earlier segments are in the running sums
 
-    for (int s0 = sb; s0 < se; s0 += SC) {
+    for (int s0 = sb; SUM && s0 < se; s0 += SC) {
         const int sc = min(SC, se - s0);
         cp_async_wait_all();
         __syncthreads();
@@ -656,17 +647,8 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
             if (ext) head_chunk<true, GENERAL>(acc, S, tl, sc, geo);
             else head_chunk<false, GENERAL>(acc, S, tl, sc, geo);
         }
-        if constexpr (SEGD) {
-            nacc += sc;
-            if (nacc >= SEG && s0 + SC < se) {
-                fold_segment(P, acc, held);
-                held = true;
-                nacc = 0;
-            }
-        }
     }
-    if constexpr (SEGD)
-        if (held) unfold_segments(P, acc);
+    if constexpr (!EPI) return 0.0;
 
     // ---- epilogue: S (eq. 2), gains (eq. 1), chi^2 terms (eq. 7) ----
     float chi = 0.f;
@@ -674,12 +656,7 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     const float2 *data = reinterpret_cast<const float2 *>(P.data);
     const float *weight = reinterpret_cast<const float *>(P.weight);
     float2 *vis = reinterpret_cast<float2 *>(P.vis_out);
-    if constexpr (GRAD) {
-        for (int i = tid; i < NLOC * 8; i += THREADS) S.GG[i] = 0.f;
-        __syncthreads();
-    }
     const float2 I2[4] = {f2(1.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(1.f, 0.f)};
-    float gpsum[2][8] = {};   // gradient mode, body tiles: the two row antennas
 #pragma unroll
     for (int j = 0; j < NSLOT; j++) {
         if (!((mask >> j) & 1u)) continue;
@@ -740,36 +717,15 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
                 float4 *yo = reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(P.yout) + 4 * row);
                 yo[0] = make_float4(Y[0].x, Y[0].y, Y[1].x, Y[1].y);
                 yo[1] = make_float4(Y[2].x, Y[2].y, Y[3].x, Y[3].y);
-                const int lp = pj, lq = U.diag ? qj : U.nr + qj;
-                if (P.grad_gains) {
-#pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        if (role == 1) {        // body tile: row p for slots 0-3, p + 1 for 4-7
-                            gpsum[j >> 2][2 * c] += dGp[c].x;
-                            gpsum[j >> 2][2 * c + 1] += dGp[c].y;
-                        } else {
-                            atomicAdd(&S.GG[lp * 8 + 2 * c], dGp[c].x);
-                            atomicAdd(&S.GG[lp * 8 + 2 * c + 1], dGp[c].y);
-                        }
-                        atomicAdd(&S.GG[lq * 8 + 2 * c], dGq[c].x);
-                        atomicAdd(&S.GG[lq * 8 + 2 * c + 1], dGq[c].y);
-                    }
+                if (P.dgain) {   // this visibility's terms of the gains gradient
+                    float4 *go = reinterpret_cast<float4 *>(P.dgain) + 2 * row;
+                    const long long plane = 2ll * P.ntime * P.nbl * P.nchan;
+                    go[0] = make_float4(dGp[0].x, dGp[0].y, dGp[1].x, dGp[1].y);
+                    go[1] = make_float4(dGp[2].x, dGp[2].y, dGp[3].x, dGp[3].y);
+                    go[plane] = make_float4(dGq[0].x, dGq[0].y, dGq[1].x, dGq[1].y);
+                    go[plane + 1] = make_float4(dGq[2].x, dGq[2].y, dGq[3].x, dGq[3].y);
                 }
             }
-        }
-    }
-    if constexpr (GRAD) {
-        if (P.grad_gains && role == 1)
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-                if (mask & (0xfu << (4 * r)))
-#pragma unroll
-                    for (int c = 0; c < 8; c++) atomicAdd(&S.GG[(tl.p + r) * 8 + c], gpsum[r][c]);
-        __syncthreads();
-        for (int i = tid; P.grad_gains && i < nloc * 8; i += THREADS) {
-            const int la = i >> 3;
-            const int ant = la < U.nr ? U.r0 + la : U.c0 + (la - U.nr);
-            atomicAdd(&P.grad_gains[8 * (((long long)t * P.na + ant) * P.nchan + k) + (i & 7)], (double)S.GG[i]);
         }
     }
     double bsum = 0.0;
@@ -783,6 +739,26 @@ __device__ __forceinline__ double fused_item(const FusedParams &P, Smem &S, int 
     return bsum;
 }
 
+// The source sum of [sb, se) into acc: one FP32 sum for lists of up to
+// 2 SEG sources, else segments of SEG sources folded into the block's running
+// sums (P.segsum) between them. Every kernel that sums a source list goes
+// through here, so a list's sums do not depend on the kernel that ran it.
+template <int MODE, bool GENERAL>
+__device__ __forceinline__ void source_sum(const FusedParams &P, Smem &S, int t, int k, int u, int sb, int se,
+                                           Pair (&acc)[NSLOT / 2]) {
+    const int len = se - sb > 2 * SEG ? SEG : se - sb;
+    bool held = false;
+    for (int s0 = sb;; s0 += len) {
+        const int s1 = min(s0 + len, se);
+        zero_sums(acc);
+        fused_item<MODE, GENERAL, true, false>(P, S, t, k, u, s0, s1, acc);
+        if (s1 >= se) break;
+        fold_segment(P, acc, held);
+        held = true;
+    }
+    if (held) unfold_segments(P, acc);
+}
+
 template <int MODE, bool GENERAL>
 __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(const FusedParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -793,7 +769,9 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32(cons
     const int rest = blockIdx.x / P.nunits;
     const int k = rest % P.nchan;
     const int t = P.t_begin + rest / P.nchan;
-    const double bsum = fused_item<MODE, GENERAL>(P, S, t, k, u, P.src0, P.src1);
+    Pair acc[NSLOT / 2];
+    zero_sums(acc);
+    const double bsum = fused_item<MODE, GENERAL, true, true>(P, S, t, k, u, P.src0, P.src1, acc);
     if constexpr (MODE != MODE_PREDICT) finish_chi2<THREADS>(bsum, P, S.red, &sLast);
 }
 
@@ -812,7 +790,9 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_fused_f32_seg(
         const long long rest = item / P.nunits;
         const int k = (int)(rest % P.nchan);
         const int t = P.t_begin + (int)(rest / P.nchan);
-        const double bsum = fused_item<MODE, GENERAL, true>(P, S, t, k, u, P.src0, P.src1);
+        Pair acc[NSLOT / 2];
+        source_sum<MODE, GENERAL>(P, S, t, k, u, P.src0, P.src1, acc);
+        const double bsum = fused_item<MODE, GENERAL, false, true>(P, S, t, k, u, P.src0, P.src1, acc);
         if (MODE != MODE_PREDICT && threadIdx.x == 0) P.partials[item] = bsum;
     }
     if constexpr (MODE == MODE_PREDICT) return;
@@ -863,7 +843,9 @@ __global__ void __launch_bounds__(THREADS, RIME_F32_MIN_BLOCKS) k_batched_f32(co
         for (int rank = g * B.gsets; rank < r1; rank++) {
             const int j = B.order[rank];
             for (int k = kc * B.cpi; k < k1; k++) {
-                const double bsum = fused_item<MODE_CHI2, GENERAL>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1]);
+                Pair acc[NSLOT / 2];
+                source_sum<MODE_CHI2, GENERAL>(P, S, t, k, u, B.offsets[j], B.offsets[j + 1], acc);
+                const double bsum = fused_item<MODE_CHI2, GENERAL, false, true>(P, S, t, k, u, 0, 0, acc);
                 if (threadIdx.x == 0)
                     B.partials[(long long)j * B.per_set + ((long long)t * P.nchan + k) * P.nunits + u] = bsum;
                 __syncthreads();
@@ -992,7 +974,7 @@ cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2) 
 }
 
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
-                        double *grad_gains) {
+                       void *dgain) {
     P.na = c->dims.na;
     P.ntime = c->dims.ntime;
     P.nchan = c->dims.nchan;
@@ -1023,35 +1005,41 @@ void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double 
     P.result = result;
     P.status = c->d_status;
     P.yout = yout;
-    P.grad_gains = grad_gains;
+    P.dgain = dgain;
     P.src0 = 0;
     P.src1 = c->nsrc;
     P.t_begin = 0;
 }
 
 cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
-                              double *grad_gains) {
+                              void *dgain) {
     FusedParams P{};
-    fill_fused_params(c, P, vis_out, result, yout, grad_gains);
+    fill_fused_params(c, P, vis_out, result, yout, dgain);
     return launch_tiled_params(c, mode, P, fused_blocks(c));
 }
 
 long long seg_source_threshold() { return 2 * f32::SEG; }
 size_t seg_scratch_per_block() { return (size_t)2 * 64 * f32::THREADS * sizeof(float); }
 
-// Long source lists (FP32): the persistent kernel with per-block running sums.
-static cudaError_t launch_seg_f32(rime_ctx *c, int mode, const FusedParams &P, long long nitems, cudaStream_t stream) {
-    const size_t per_block = seg_scratch_per_block();
+// The running sums of long FP32 source lists: one scratch slot per resident
+// block of a persistent grid (the context's own, or the caller's in a view).
+cudaError_t ensure_segsum(rime_ctx *c) {
     if (c->nsm <= 0 && cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         c->nsm = 152;
     if (!c->d_segsum && !c->view) {
         Alloc alloc{c};
         const size_t nb = (size_t)c->nsm * RIME_F32_MIN_BLOCKS;
-        cudaError_t e = alloc((void **)&c->d_segsum, per_block * nb);
+        cudaError_t e = alloc((void **)&c->d_segsum, seg_scratch_per_block() * nb);
         if (e != cudaSuccess) return e;
         c->segsum_blocks = nb;
     }
-    if (!c->d_segsum || c->segsum_blocks == 0) return cudaErrorInvalidValue;
+    return c->d_segsum && c->segsum_blocks > 0 ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Long source lists (FP32): the persistent kernel with per-block running sums.
+static cudaError_t launch_seg_f32(rime_ctx *c, int mode, const FusedParams &P, long long nitems, cudaStream_t stream) {
+    cudaError_t e0 = ensure_segsum(c);
+    if (e0 != cudaSuccess) return e0;
     FusedParams Q = P;
     Q.segsum = c->d_segsum;
     const long long grid = std::min<long long>(nitems, (long long)c->segsum_blocks);
@@ -1101,6 +1089,12 @@ cudaError_t launch_batched_f32(rime_ctx *c, const BatchParams &B, int grid) {
     FusedParams P{};
     fill_fused_params(c, P, nullptr, nullptr, nullptr, nullptr);
     if (grid <= 0 || B.nitems == 0) return cudaSuccess;
+    if (B.max_set > seg_source_threshold()) {   // long sets fold into per-block running sums
+        cudaError_t e = ensure_segsum(c);
+        if (e != cudaSuccess) return e;
+        P.segsum = c->d_segsum;
+        grid = (int)std::min<long long>(grid, (long long)c->segsum_blocks);
+    }
     const size_t sm = sizeof(f32::Smem);
     auto kern = (c->beam_model != RIME_BEAM_COS3 || c->has_kind) ? f32::k_batched_f32<true>
                                                                   : f32::k_batched_f32<false>;

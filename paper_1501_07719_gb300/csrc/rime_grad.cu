@@ -20,6 +20,7 @@
 // in a fixed order.
 #include "rime_internal.cuh"
 #include "rime_beam.cuh"
+#include "rime_fused_common.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -373,7 +374,10 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
 // group grp of 16); the pair's z, Gaussian factors and moments are computed
 // on packed FP32 pairs (one instruction for both sources), the baseline data
 // and Y_X are shared by the pair. Same staging, moments and channel factors as
-// k_grad_src.
+// k_grad_src, with the per-antenna factors of a source pair staged as
+// (re, re', im, im') (one load gives both pairs) and each thread's next
+// baseline found by arithmetic along the row-major baseline list, so that
+// the factor loads do not wait for a table load.
 __device__ __forceinline__ float2 pf2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 pdup(float a) { return make_float2(a, a); }
 
@@ -464,6 +468,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
         for (int i = 0; i < NGRAD; i++) out[h][i] = 0.f;
 
     const int nchunk = (nb + BLC - 1) / BLC;
+    const int qend = U.diag ? U.nr : U.nc, cofs = U.diag ? 0 : U.nr;   // columns of a row; their offset
     auto issue_y = [&](int j) {
         const int kk = k0 + j / nchunk, b0 = (j % nchunk) * BLC;
         const int cnt = min(BLC, nb - b0);
@@ -498,9 +503,13 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 T2 d;
                 d.x = t3 * ch.cnu * ch.cnu * (exq[0] - (T)ptab[2 * ant]);
                 d.y = t3 * ch.cnu * ch.cnu * (exq[1] - (T)ptab[2 * ant + 1]);
-                sE[i] = d;
+                float *oe = reinterpret_cast<float *>(sE) + 2 * (i & ~1) + (i & 1);
+                oe[0] = d.x;
+                oe[2] = d.y;
             }
-            sA[i] = v;
+            float *o = reinterpret_cast<float *>(sA) + 2 * (i & ~1) + (i & 1);   // (re, re', im, im')
+            o[0] = v.x;
+            o[2] = v.y;
         }
         const float4 gq0 = reinterpret_cast<const float4 *>(P.gauss)[sidx[0]];
         const float4 gq1 = reinterpret_cast<const float4 *>(P.gauss)[sidx[1]];
@@ -516,16 +525,29 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
             __syncthreads();
             if (job + 1 < njobs) issue_y(job + 1);
             const T2 *yb = sY + (job & 1) * BLC * 4;
+            // local (row, column) of this thread's baseline b0 + i
+            int pl = 0, ql = 0;
+            if (grp < cnt) {
+                const uint16_t e = bls[b0 + grp];
+                pl = e & 0xff;
+                ql = e >> 8;
+            }
 #pragma unroll 2
             for (int i = grp; i < cnt; i += NG) {
                 const float4 bb = *reinterpret_cast<const float4 *>(sB + 4 * (b0 + i));
                 const T du = bb.x, dv = bb.y, dw = bb.z;
-                const int pq = __float_as_int(bb.w);
-                const int oa = pq & 0xffff, ob = pq >> 16;
+                const int oa = pl * SG, ob = (cofs + ql) * SG;
                 const float4 ap = *reinterpret_cast<const float4 *>(sA + oa + 2 * sp);
                 const float4 aq = *reinterpret_cast<const float4 *>(sA + ob + 2 * sp);
-                const float2 apr = pf2(ap.x, ap.z), api = pf2(ap.y, ap.w);
-                const float2 aqr = pf2(aq.x, aq.z), aqi = pf2(aq.y, aq.w);
+                if (i + NG < cnt) {   // the next baseline of this thread (it exists: the walk ends)
+                    ql += NG;
+                    for (int w = 0; w < GNLOC && ql >= qend; w++) {
+                        pl++;
+                        ql -= qend - (U.diag ? pl + 1 : 0);
+                    }
+                }
+                const float2 apr = pf2(ap.x, ap.y), api = pf2(ap.z, ap.w);
+                const float2 aqr = pf2(aq.x, aq.y), aqi = pf2(aq.z, aq.w);
                 // z = A_p conj(A_q) for both sources
                 float2 zr = __ffma2_rn(apr, aqr, __fmul2_rn(api, aqi));
                 float2 zi = __ffma2_rn(api, aqr, __fmul2_rn(pf2(-apr.x, -apr.y), aqi));
@@ -535,12 +557,12 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                     float2 g;
                     if (any_disk) {
                         const float r0 = rsqrtf(1.f + e.x), r1 = rsqrtf(1.f + e.y);
-                        g.x = is_disk[0] ? r0 * r0 * r0 : exp2f(e.x);
-                        g.y = is_disk[1] ? r1 * r1 * r1 : exp2f(e.y);
+                        g.x = is_disk[0] ? r0 * r0 * r0 : ex2_approx(e.x);
+                        g.y = is_disk[1] ? r1 * r1 * r1 : ex2_approx(e.y);
                         hq.x = is_disk[0] ? -1.5f * r0 * r0 : 1.f;
                         hq.y = is_disk[1] ? -1.5f * r1 * r1 : 1.f;
                     } else {
-                        g = pf2(exp2f(e.x), exp2f(e.y));
+                        g = pf2(ex2_approx(e.x), ex2_approx(e.y));   // the forward kernels' exp2
                     }
                     zr = __fmul2_rn(zr, g);
                     zi = __fmul2_rn(zi, g);
@@ -570,8 +592,8 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
                 if (pointing) {
                     const float4 ep = *reinterpret_cast<const float4 *>(sE + oa + 2 * sp);
                     const float4 eq = *reinterpret_cast<const float4 *>(sE + ob + 2 * sp);
-                    acc[10] = __ffma2_rn(re, pf2(ep.x + eq.x, ep.z + eq.z), acc[10]);
-                    acc[11] = __ffma2_rn(re, pf2(ep.y + eq.y, ep.w + eq.w), acc[11]);
+                    acc[10] = __ffma2_rn(re, pf2(ep.x + eq.x, ep.y + eq.y), acc[10]);
+                    acc[11] = __ffma2_rn(re, pf2(ep.z + eq.z, ep.w + eq.w), acc[11]);
                 }
             }
         }
@@ -890,7 +912,69 @@ __global__ void k_colsum(long long nrows, long long ncols, long long rpb, const 
     }
 }
 
+// d chi^2 / dG per (t, antenna a, channel k, Jones entry) from the terms the
+// forward kernel stored per visibility row (t, baseline, k): the dG_q terms
+// of the baselines (p, a), p ascending, then the dG_p terms of (a, q), q
+// ascending, summed in the context's precision (the terms carry its rounding
+// already; at most na - 1 of them). One thread per (t, a, k), k fastest, so
+// that a warp reads one baseline's rows of consecutive channels from one
+// plane; the order of the sum is fixed, and the result bit-reproducible.
+template <typename T>
+__device__ __forceinline__ void add_terms(T (&s)[8], const T *r) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[i] += __ldcs(r + i);
+}
+template <>
+__device__ __forceinline__ void add_terms<float>(float (&s)[8], const float *r) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(r)), b = __ldcs(reinterpret_cast<const float4 *>(r) + 1);
+    s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w;
+    s[4] += b.x; s[5] += b.y; s[6] += b.z; s[7] += b.w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gains_grad(int na, int nchan, long long nbl, long long n, const T *dg,
+                                                   long long plane, double *gg, const DevStatus *status) {
+    if (inputs_bad(status)) return;
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const int k = (int)(i % nchan);
+        const long long ta = i / nchan;
+        const int a = (int)(ta % na);
+        const long long t = ta / na;
+        const T *dgp = dg + 8 * (t * nbl * nchan + k);      // plane 0, row (t, baseline 0, k)
+        const T *dgq = dgp + plane;                         // plane 1
+        const long long bstride = 8ll * nchan;              // the next baseline's row
+        T s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int p = 0; p < a; p++) {
+            const long long bl = (long long)p * na - (long long)p * (p + 1) / 2 + (a - p - 1);
+            add_terms<T>(s, dgq + bl * bstride);
+        }
+        const long long b0 = (long long)a * na - (long long)a * (a + 1) / 2;   // baseline (a, a + 1)
+        for (int q = a + 1; q < na; q++) add_terms<T>(s, dgp + (b0 + (q - a - 1)) * bstride);
+        double2 *o = reinterpret_cast<double2 *>(gg + 8 * i);
+#pragma unroll
+        for (int c = 0; c < 4; c++) o[c] = make_double2((double)s[2 * c], (double)s[2 * c + 1]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gains_grad(rime_ctx *c, double *grad_gains) {
+    const long long n = (long long)c->dims.ntime * c->dims.na * c->dims.nchan;
+    if (n == 0) return cudaSuccess;
+    if (c->nsm <= 0 && cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        c->nsm = 152;
+    const long long grid = std::min<long long>((n + 255) / 256, (long long)c->nsm * 16);
+    const long long plane = 8ll * c->dims.ntime * c->nbl * c->dims.nchan;   // elements per plane
+    if (c->dims.precision == RIME_FP64)
+        k_gains_grad<double><<<(unsigned)grid, 256, 0, c->stream>>>(c->dims.na, c->dims.nchan, c->nbl, n,
+                                                                    static_cast<const double *>(c->d_dgain), plane,
+                                                                    grad_gains, c->d_status);
+    else
+        k_gains_grad<float><<<(unsigned)grid, 256, 0, c->stream>>>(c->dims.na, c->dims.nchan, c->nbl, n,
+                                                                  static_cast<const float *>(c->d_dgain), plane,
+                                                                  grad_gains, c->d_status);
+    return cudaGetLastError();
+}
 
 // Gradient work units: the FP32 forward decomposition, with each unit's
 // baselines listed as (p | q << 8) local antenna pairs.

@@ -120,7 +120,9 @@ struct FusedParams {
     const DevStatus *status;   // kernels skip their work if any err word is set
     // gradient mode only
     void *yout;                // complex T [ntime][nbl][nchan][4]: Stokes-projected adjoint Y_X
-    double *grad_gains;        // complex128 [ntime][na][nchan][4], accumulated (zeroed before)
+    void *dgain;               // T [2][ntime][nbl][nchan][8] or null: per visibility the terms of the
+                               // gains gradient, d chi^2 / dG_p (plane 0) and d chi^2 / dG_q (plane 1),
+                               // 4 complex each
     int src0, src1;            // the source range [src0, src1) of this launch (default: all)
     int t_begin;               // first timestep of the launch (the grid covers a time range)
     float *segsum;             // FP32 tile kernel, long source lists: per-block running sums
@@ -137,6 +139,7 @@ struct BatchParams {
     const int *offsets;        // [nsets + 1] source offsets
     unsigned long long *counter;   // next work item (zeroed before the launch)
     double *partials;          // [nsets][ntime][nchan][nunits]
+    int max_set;               // sources of the largest set (host side: scratch for long lists)
 };
 
 // Kernel modes of the fused predict / chi^2 kernels.
@@ -194,6 +197,7 @@ struct rime_ctx {
     void *d_src_extra = nullptr;      // per source: l, m, l/n, m/n, major, minor, sin pa, cos pa
     // gradient scratch (allocated by the first rime_chi2_grad)
     void *d_yadj = nullptr;           // Y_X per visibility
+    void *d_dgain = nullptr;          // per visibility the two terms of the gains gradient (16 T)
     double *d_gpart = nullptr;        // per (t, k, unit) partial source gradients
     size_t gpart_cap = 0;
     rime::Unit *d_gunits = nullptr;   // gradient work units and their baseline lists
@@ -284,10 +288,12 @@ cudaError_t launch_validate_chunk(rime_ctx *c, long long nvis, const void *data,
                                   long long i0, cudaStream_t stream = nullptr);
 // rime_grad.cu
 cudaError_t launch_grad_src(rime_ctx *c, double *grad_src);
+// the gains gradient from the per-visibility terms: a fixed-order sum per (t, antenna, channel)
+cudaError_t launch_gains_grad(rime_ctx *c, double *grad_gains);
 // launchers (rime_fused.cu)
 cudaError_t launch_fused(rime_ctx *c, void *vis_out, double *result, bool chi2);
 cudaError_t launch_fused_mode(rime_ctx *c, int mode, void *vis_out, double *result, void *yout,
-                              double *grad_gains);
+                              void *dgain);
 int fused_blocks(const rime_ctx *c);
 int build_units_fixed(int na, int precision, Unit *units, int max_units, Tile *tiles, int max_tiles,
                       int *ntiles);
@@ -298,9 +304,10 @@ cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *resu
 // FP32 source lists longer than this run the persistent kernel with per-block
 // running sums of this many bytes per block (rime_fused.cu)
 long long seg_source_threshold();
+cudaError_t ensure_segsum(rime_ctx *c);
 size_t seg_scratch_per_block();
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
-                       double *grad_gains);
+                       void *dgain);
 // launches the tiled fused kernel of `mode` with prepared parameters over `blocks` blocks
 // (stream: nullptr = the context's stream)
 cudaError_t launch_tiled_params(rime_ctx *c, int mode, const FusedParams &P, long long blocks,
@@ -310,7 +317,7 @@ constexpr int NARROW_MAX_NA = 45;      // it takes arrays of up to this many ant
 constexpr int NARROW_AUTO_NA_F32 = 32; // RIME_KERNEL_AUTO picks it up to here in FP32 (FP64: 45)
 bool narrow_applies(const rime_ctx *c);
 cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1,
-                          void *yout = nullptr, double *grad_gains = nullptr);
+                          void *yout = nullptr, void *dgain = nullptr);
 // the same with prepared parameters over timesteps [P.t_begin, P.t_begin + nt)
 cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, int nt,
                                  cudaStream_t stream = nullptr);

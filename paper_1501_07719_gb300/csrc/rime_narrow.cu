@@ -77,13 +77,12 @@ static Shape shape_for(int na, int ntime, int nchan, int nsm) {
 }
 
 template <typename T>
-static size_t smem_bytes(int na, int cg, bool grad) {
+static size_t smem_bytes(int na, int cg) {
     using C = Cfg<T>;
     return (size_t)cg * C::SC * na * sizeof(typename C::T2)      // K (times E) per (channel, source, antenna)
            + (size_t)cg * C::SC * sizeof(typename C::T4)         // scaled Stokes per (channel, source)
            + (size_t)C::SC * sizeof(typename C::T4)              // Gaussian coefficients per source
-           + 32 * sizeof(double)                                 // reduction scratch
-           + (grad ? (size_t)cg * na * 8 * sizeof(double) : 0);  // gains gradient per (channel, antenna)
+           + 32 * sizeof(double);                                // reduction scratch
 }
 
 // K = exp(2 pi i nu tau) for the delay stored for (t, s, a).
@@ -133,7 +132,6 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
     T4 *sSt = reinterpret_cast<T4 *>(sA + (size_t)cg * SC * na);     // [cg][SC]
     T4 *sG = sSt + cg * SC;                                          // [SC]
     double *sRed = reinterpret_cast<double *>(sG + SC);              // [32]
-    double *sGG = sRed + 32;                                         // gradient mode: [cg][na][8]
     __shared__ int sLast;
 
     if (inputs_bad(P.status)) return;
@@ -192,9 +190,6 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
     for (int i = 0; i < M; i++)
 #pragma unroll
         for (int c = 0; c < 8; c++) acc[i][c] = T(0);
-    if constexpr (GRAD) {
-        for (int i = tid; i < cg * na * 8; i += THREADS) sGG[i] = 0.0;   // ordered by the first barrier below
-    }
 
     const auto *tau = reinterpret_cast<const typename std::conditional<sizeof(T) == 4, float2, double>::type *>(P.tau);
     const T *rho = reinterpret_cast<const T *>(P.rho);
@@ -316,24 +311,16 @@ __global__ void __launch_bounds__(THREADS) k_narrow(const FusedParams P, const i
                 T2 *yo = reinterpret_cast<T2 *>(P.yout) + 4 * row;
 #pragma unroll
                 for (int c = 0; c < 4; c++) yo[c] = Y[c];
-                if (P.grad_gains) {
-                    double *gpp = sGG + ((k - k0) * na + p) * 8, *gqq = sGG + ((k - k0) * na + q) * 8;
+                if (P.dgain) {   // this visibility's terms of the gains gradient
+                    T2 *go = reinterpret_cast<T2 *>(P.dgain) + 4 * row;
+                    const long long plane = 4ll * P.ntime * P.nbl * P.nchan;
 #pragma unroll
                     for (int c = 0; c < 4; c++) {
-                        atomicAdd(gpp + 2 * c, (double)dGp[c].x);
-                        atomicAdd(gpp + 2 * c + 1, (double)dGp[c].y);
-                        atomicAdd(gqq + 2 * c, (double)dGq[c].x);
-                        atomicAdd(gqq + 2 * c + 1, (double)dGq[c].y);
+                        go[c] = dGp[c];
+                        go[plane + c] = dGq[c];
                     }
                 }
             }
-        }
-    }
-    if constexpr (GRAD) {
-        __syncthreads();
-        for (int i = tid; P.grad_gains && i < ncg * na * 8; i += THREADS) {
-            const int ca = i >> 3, c = ca / na, a = ca - c * na;
-            atomicAdd(&P.grad_gains[8 * (((long long)t * na + a) * P.nchan + k0 + c) + (i & 7)], sGG[i]);
         }
     }
     if constexpr (CHI2) {
@@ -376,9 +363,9 @@ bool narrow_applies(const rime_ctx *c) {
 }
 
 cudaError_t launch_narrow(rime_ctx *c, int mode, void *vis_out, double *result, int src0, int src1, void *yout,
-                          double *grad_gains) {
+                          void *dgain) {
     FusedParams P{};
-    fill_fused_params(c, P, vis_out, result, yout, grad_gains);
+    fill_fused_params(c, P, vis_out, result, yout, dgain);
     P.src0 = src0;
     P.src1 = src1;
     return launch_narrow_params(c, mode, P, c->dims.ntime);
@@ -400,8 +387,7 @@ cudaError_t launch_narrow_params(rime_ctx *c, int mode, const FusedParams &P, in
     if (blocks == 0) return cudaSuccess;
     if (blocks > (long long)c->partials_cap) return cudaErrorInvalidValue;   // cannot happen: <= fused blocks
     const bool f64 = c->dims.precision == RIME_FP64;
-    const bool grad = mode == MODE_GRAD;
-    const size_t smem = f64 ? smem_bytes<double>(c->dims.na, s.cg, grad) : smem_bytes<float>(c->dims.na, s.cg, grad);
+    const size_t smem = f64 ? smem_bytes<double>(c->dims.na, s.cg) : smem_bytes<float>(c->dims.na, s.cg);
     if (f64) return launch_shape<double>(P, mode, s, (int)blocks, smem, stream);
     return launch_shape<float>(P, mode, s, (int)blocks, smem, stream);
 }
