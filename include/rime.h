@@ -200,9 +200,10 @@ typedef enum {
  * FP64 value of the reduced argument to within one FP32 unit of 1/2, see
  * rime_phase_turns), and the chi^2 is summed in FP64. Errors against the FP64
  * result on 256 antennas, 128 channels and 4096 point sources (|V| ~ 1e2 Jy,
- * residuals at a 0.01 Jy noise level): BF16 3.9e-6 of the largest
- * visibility and 7.1e-4 of chi^2 (above an FP32 bound of 1e-4); TF32 6.6e-7
- * and 1.4e-5.
+ * residuals at a 0.01 Jy noise level; 192 sampled visibilities, chi^2 on one
+ * timestep and two channels): BF16 5.7e-6 of the largest visibility and
+ * 7.3e-4 of chi^2 (above an FP32 bound of 1e-4); TF32 1.2e-6 and 2.6e-5
+ * (within it).
  * The split modes take point sources only: a sky model with a Gaussian
  * source makes the next waiting call return RIME_E_INVALID. rime_chi2_grad
  * and rime_chi2_batched always use the direct FP32 path.

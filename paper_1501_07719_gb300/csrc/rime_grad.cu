@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
         const ChanF ch = reinterpret_cast<const ChanF *>(P.chan)[k];
         __syncthreads();
         for (int i = tid; i < nloc * SG; i += GTHREADS) {
-            T2 v = phase(rTau + i, 0, ch);
+            T2 v = f32::phase_factor(rTau[i], ch);   // the forward kernels' K
             if (pointing) {
                 const int a = i / SG, ss = i - a * SG;
                 const int src = min(sch * SG + ss, P.nsrc - 1);

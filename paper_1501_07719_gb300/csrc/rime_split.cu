@@ -61,10 +61,22 @@ constexpr int NPROD = NDRAIN + 128;     // and four warps of B producers
 constexpr int THREADS = NPROD + 128;    // and a warpgroup whose first warp issues the MMAs
 constexpr int NST = 8;                  // pipeline stages
 // registers per thread: at launch (65536 / THREADS), then per warpgroup
-// A (two warpgroups: 128 running sums each), B, MMA: 2*128*200 + 128*88 +
-// 128*24 = 65536 = 128 * 512
-constexpr int REGS_LAUNCH = 128, REGS_A = 200, REGS_B = 88, REGS_MMA = 24;
-static_assert(2 * 128 * REGS_A + 128 * REGS_B + 128 * REGS_MMA <= REGS_LAUNCH * THREADS, "register split");
+// A (two warpgroups: 128 running sums each), B, MMA, e.g. 2*128*200 +
+// 128*88 + 128*24 = 65536 = 128 * 512
+// (BF16: 208 for A, 72 for B; TF32, whose B threads need more: 200 and 88)
+#ifndef RIME_SPLIT_REGS_A_BF16
+#define RIME_SPLIT_REGS_A_BF16 208
+#endif
+#ifndef RIME_SPLIT_REGS_A_TF32
+#define RIME_SPLIT_REGS_A_TF32 200
+#endif
+constexpr int REGS_LAUNCH = 128, REGS_MMA = 24;
+template <bool TF32> struct Regs {
+    static constexpr int A = TF32 ? RIME_SPLIT_REGS_A_TF32 : RIME_SPLIT_REGS_A_BF16;
+    static constexpr int B = (REGS_LAUNCH * THREADS - 2 * 128 * A - 128 * REGS_MMA) / 128 / 8 * 8;
+    static_assert(2 * 128 * A + 128 * B + 128 * REGS_MMA <= REGS_LAUNCH * THREADS, "register split");
+    static_assert(A % 8 == 0 && A <= 256 && B >= 24 && B <= REGS_LAUNCH, "setmaxnreg range");
+};
 constexpr int SEG = 8;                  // stages accumulated in TMEM before a drain
 constexpr uint32_t A_BYTES = tc::operand_bytes(PT);
 constexpr uint32_t B_BYTES = tc::operand_bytes(NB);
@@ -551,10 +563,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
                 nstg, (nstg + SEG - 1) / SEG, P.chan[k]};
     double chi = 0.0;
     if (warp < NDRAIN / 32) {
-        tc::regs_inc<REGS_A>();
+        tc::regs_inc<Regs<TF32>::A>();
         chi = role_a<TF32, WRITE>(C, tid, warp, lane);
     } else if (warp < NPROD / 32) {
-        tc::regs_dec<REGS_B>();
+        tc::regs_dec<Regs<TF32>::B>();
         role_b<TF32>(C, warp, lane);
     } else {
         tc::regs_dec<REGS_MMA>();
