@@ -387,7 +387,7 @@ __device__ __forceinline__ float2 shape2(const float4 &q, const Geo &G, int h) {
 template <bool SHAPE, bool GENERAL>
 __device__ __forceinline__ void body_chunk(Pair (&acc)[NSLOT / 2], const Smem &S, const float *KxC, const float *KyC,
                                            int cstr, int ip, int iq, int sc, const Geo &G) {
-#pragma unroll 1
+#pragma unroll 2
     for (int s = 0; s < sc; s++) {
         const float2 kr = *reinterpret_cast<const float2 *>(S.Kx + s * RSTR + ip);
         const float2 ki = *reinterpret_cast<const float2 *>(S.Ky + s * RSTR + ip);
@@ -416,7 +416,7 @@ __device__ __forceinline__ void head_chunk(Pair (&acc)[NSLOT / 2], const Smem &S
     int ho[8];   // shared-memory offsets of x_0..x_7 (one 8-antenna block)
 #pragma unroll
     for (int i = 0; i < 8; i++) ho[i] = hb + ((r + i) & 7);
-#pragma unroll 1
+#pragma unroll 2
     for (int s = 0; s < sc; s++) {
         const float4 x = S.St[s];
         const float2 X[4] = {f2(x.x, x.x), f2(x.y, x.y), f2(x.z, x.z), f2(x.w, x.w)};
