@@ -244,31 +244,44 @@ def form_sampler(torch, R):
     return out
 
 
-def form_grad(torch, R, chi2_ms):
-    """Adjoint gradient (rime_chi2_grad) on the 64-antenna gradient workload,
-    against the plain fused chi^2 of the same workload."""
-    wl = rime_synth.WORKLOADS["64ant-100t-64ch-100pt100g-grad"]
-    inp = rime_synth.make_inputs(wl, precision="f32")
-    w = inp["weight"].astype(np.float32)
-    ctx = R.Rime(inp, R.RIME_FP32, weight=w)
+def _grad_times(torch, R, wl, precision, reps):
+    """(chi^2 + gradient ms, plain chi^2 ms) of one workload in one precision."""
+    f64 = precision == "f64"
+    inp = rime_synth.make_inputs(wl, precision=precision)
+    w = inp["weight"] if f64 else inp["weight"].astype(np.float32)
+    ctx = R.Rime(inp, R.RIME_FP64 if f64 else R.RIME_FP32, weight=w)
     ctx.set_gains(inp["gains"])
     ctx.set_sources(inp["sources"])
     V = ctx.predict()
-    ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex64), w)
+    D = V.cpu().numpy().astype(np.complex128) + inp["noise"]
     del V
+    ctx.set_data(D if f64 else D.astype(np.complex64), w)
     stream = torch.cuda.current_stream()
     gs = torch.zeros((wl.nsrc, 10), dtype=torch.float64, device="cuda")
     gg = torch.zeros((wl.ntime, wl.na, wl.nchan, 2, 2), dtype=torch.complex128, device="cuda")
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
-    for _ in range(2):
+    R.rime_chi2_grad(ctx.ctx, gs, gg)
+    if not f64:
         R.rime_chi2_grad(ctx.ctx, gs, gg)
-    grad_ms = _timed(torch, stream, lambda: R.rime_chi2_grad(ctx.ctx, gs, gg), 5)
-    plain_ms = _timed(torch, stream, lambda: ctx.chi2_async(out), 20)
+    grad_ms = _timed(torch, stream, lambda: R.rime_chi2_grad(ctx.ctx, gs, gg), reps)
+    ctx.chi2_async(out)
+    plain_ms = _timed(torch, stream, lambda: ctx.chi2_async(out), 4 * reps)
     ctx.close()
+    return grad_ms, plain_ms
+
+
+def form_grad(torch, R, chi2_ms):
+    """Adjoint gradient (rime_chi2_grad) on the 64-antenna gradient workload,
+    against the plain fused chi^2 of the same workload, in FP32 (the top-level
+    keys) and FP64."""
+    wl = rime_synth.WORKLOADS["64ant-100t-64ch-100pt100g-grad"]
+    grad_ms, plain_ms = _grad_times(torch, R, wl, "f32", 5)
+    g64, p64 = _grad_times(torch, R, wl, "f64", 2)
     nparam = 10 * wl.nsrc
     return {"workload": wl.name, "dtype": "f32", "chi2_grad_ms": grad_ms, "chi2_ms": plain_ms,
             "grad_over_chi2": grad_ms / plain_ms,
             "speedup_vs_central_fd_of_source_params": 2 * nparam * plain_ms / grad_ms,
+            "f64": {"chi2_grad_ms": g64, "chi2_ms": p64, "grad_over_chi2": g64 / p64},
             "fd_basis": f"central differences need 2 x {nparam} chi^2 evaluations for the source "
                         "parameters alone; the adjoint also returns the gains gradient",
             "outputs": "chi^2, d/d(l, m, I, Q, U, V, alpha, major, minor, pa) per source, d/dG per "
