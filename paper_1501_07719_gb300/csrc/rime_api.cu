@@ -67,7 +67,7 @@ void free_all(rime_ctx *c) {
                     c->d_gunits, c->d_gbl, c->d_bsched, c->d_bpart, c->d_bcounter, c->d_stiles,
                     c->d_spart, c->d_scounter, c->d_sscale, c->d_schi,
                     c->d_chainN, c->d_chain_scratch, c->d_pair, c->d_pair_kind, c->d_chain_part, c->d_segsum,
-                    c->d_dgain};
+                    c->d_dgain, c->d_segsum2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : c->d_sbuf)

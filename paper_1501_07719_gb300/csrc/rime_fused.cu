@@ -1035,13 +1035,23 @@ cudaError_t ensure_segsum(rime_ctx *c) {
     }
     return c->d_segsum && c->segsum_blocks > 0 ? cudaSuccess : cudaErrorInvalidValue;
 }
+cudaError_t ensure_segsum2(rime_ctx *c) {
+    cudaError_t e = ensure_segsum(c);
+    if (e != cudaSuccess) return e;
+    if (!c->d_segsum2 && !c->view) {
+        Alloc alloc{c};
+        e = alloc((void **)&c->d_segsum2, seg_scratch_per_block() * c->segsum_blocks);
+        if (e != cudaSuccess) return e;
+    }
+    return c->d_segsum2 ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 // Long source lists (FP32): the persistent kernel with per-block running sums.
 static cudaError_t launch_seg_f32(rime_ctx *c, int mode, const FusedParams &P, long long nitems, cudaStream_t stream) {
     cudaError_t e0 = ensure_segsum(c);
     if (e0 != cudaSuccess) return e0;
     FusedParams Q = P;
-    Q.segsum = c->d_segsum;
+    if (!Q.segsum) Q.segsum = c->d_segsum;   // a caller running launches side by side gives its own
     const long long grid = std::min<long long>(nitems, (long long)c->segsum_blocks);
     const size_t sm = sizeof(f32::Smem);
     auto go = [&](auto kernel) -> cudaError_t {

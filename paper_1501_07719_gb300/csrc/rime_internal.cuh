@@ -231,7 +231,8 @@ struct rime_ctx {
     int nsm = 0;
     unsigned long long wait_ns = 0;   // limit of the kernels' bounded waits (0: about two seconds)
     float *d_segsum = nullptr;        // FP32 tile kernel: running sums of long source lists, per block
-    size_t segsum_blocks = 0;         // blocks it holds
+    float *d_segsum2 = nullptr;       // the same for the streamed chi^2's second kernel stream
+    size_t segsum_blocks = 0;         // blocks each holds
     bool view = false;                // a view over caller memory (rime_chi2_noalloc): allocates nothing
     // tensor-core split-precision mode (FP32 contexts)
     int tc_mode = 0;                  // rime_tc_mode
@@ -305,6 +306,9 @@ cudaError_t launch_fused_f64_range(rime_ctx *c, int src0, int src1, double *resu
 // running sums of this many bytes per block (rime_fused.cu)
 long long seg_source_threshold();
 cudaError_t ensure_segsum(rime_ctx *c);
+// a second scratch of the same size, for launches that may run beside those
+// using the first (the streamed chi^2's second kernel stream)
+cudaError_t ensure_segsum2(rime_ctx *c);
 size_t seg_scratch_per_block();
 void fill_fused_params(const rime_ctx *c, FusedParams &P, void *vis_out, double *result, void *yout,
                        void *dgain);

@@ -174,6 +174,10 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
     const long long bpt = narrow ? narrow_blocks_per_time(c) : (long long)c->dims.nchan * c->nunits;
     if ((long long)ntime * bpt > (long long)c->partials_cap)
         return fail_ctx(c, RIME_E_INVALID, "internal: block partials exceed their buffer");
+    // long FP32 source lists fold into per-block running sums: the second
+    // kernel stream's chunks get their own scratch
+    const bool seg2 = !narrow && c->dims.precision == RIME_FP32 && (long long)c->nsrc > seg_source_threshold();
+    if (seg2) CKS(c, ensure_segsum2(c), "allocating the running sums of long source lists");
     const char *hd = static_cast<const char *>(data);
     const char *hw = static_cast<const char *>(weight);
     for (int i = 0; i < nchunks; i++) {
@@ -200,6 +204,7 @@ rime_status rime_chi2_streamed(rime_ctx *c, const void *data, const void *weight
         FusedParams P{};
         fill_fused_params(c, P, nullptr, c->d_schi + i, nullptr, nullptr);
         P.t_begin = t0;
+        P.segsum = seg2 && (i & 1) ? c->d_segsum2 : nullptr;   // the two streams' kernels run side by side
         P.data = reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(bd) - (uintptr_t)t0 * dbytes);
         P.weight = hw ? reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(bw) - (uintptr_t)t0 * wbytes)
                       : nullptr;

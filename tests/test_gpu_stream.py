@@ -53,6 +53,25 @@ def test_streamed_equals_resident_and_oracle(na, kernel, precision):
     r.close()
 
 
+def test_streamed_long_source_list_fp32():
+    """500 sources in FP32: every chunk kernel folds segments of its source
+    sum into per-block running sums, and the two kernel streams' chunks run
+    side by side, each with its own scratch."""
+    import torch
+    inp = make_case(rime_synth.custom(40, 6, 3, 250, 250, seed_index=47), "f32")
+    w = np.asarray(inp["weight"], dtype=np.float32)
+    r = gpu_ctx(inp, "f32")
+    resident = r.chi2()
+    cref = oracle_chi2(inp)
+    assert rel_err(resident, cref) <= TOL["f32"]["chi2"]
+    pinned_d = torch.from_numpy(np.ascontiguousarray(inp["data"])).pin_memory()
+    pinned_w = torch.from_numpy(w).pin_memory()
+    for chunk in (1, 2, 3, 0):
+        got = r.chi2_streamed(pinned_d, pinned_w, chunk)
+        assert rel_err(got, resident) <= 1e-13, (chunk, got, resident)
+    r.close()
+
+
 @pytest.mark.parametrize("kernel", [None, "tiled"])
 def test_streamed_follows_uploads_queued_before_it(kernel):
     """The chunk copies run ahead of the context's stream (a ring of up to
