@@ -381,7 +381,7 @@ def form_split(torch, R):
     csl.set_sources(inp["sources"])
     res = {}
     for mode, name in ((R.RIME_TC_OFF, "direct_fp32"), (R.RIME_TC_SPLIT_BF16, "split_bf16"),
-                       (R.RIME_TC_SPLIT_TF32, "split_tf32")):
+                       (R.RIME_TC_SPLIT_TF32, "split_tf32"), (R.RIME_TC_SPLIT_F16, "split_f16")):
         ctx.set_tensor_mode(mode)
         ctx.chi2_async(out)
         ms = _timed(torch, stream, lambda: ctx.chi2_async(out), 2 if mode == R.RIME_TC_OFF else 5)
@@ -403,7 +403,7 @@ def form_split(torch, R):
     pk = measured_peaks()
     bf16_peak = pk.get("bf16_tflops_sustained", 1700.0)
     algo = wl.ntime * wl.nchan * wl.nbl * wl.nsrc * 4 * 2 * 2 * 2 * 3
-    for name, peak in (("split_bf16", bf16_peak), ("split_tf32", bf16_peak * 1.1 / 2.25)):
+    for name, peak in (("split_bf16", bf16_peak), ("split_tf32", bf16_peak * 1.1 / 2.25), ("split_f16", bf16_peak)):
         res[name]["speedup_vs_direct"] = res["direct_fp32"]["ms"] / res[name]["ms"]
         ach = algo / (res[name]["ms"] * 1e-3) / 1e12
         res[name]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -547,9 +547,9 @@ def run_only(args):
     ctx.set_data((V.cpu().numpy().astype(np.complex128) + inp["noise"]).astype(np.complex128 if f64 else np.complex64), w)
     del V
     out = torch.zeros(max(1, wl.nsets), dtype=torch.float64, device="cuda")
-    if args.only in ("chi2", "split-bf16", "split-tf32"):
+    if args.only in ("chi2", "split-bf16", "split-tf32", "split-f16"):
         ctx.set_tensor_mode({"chi2": R.RIME_TC_OFF, "split-bf16": R.RIME_TC_SPLIT_BF16,
-                             "split-tf32": R.RIME_TC_SPLIT_TF32}[args.only])
+                             "split-tf32": R.RIME_TC_SPLIT_TF32, "split-f16": R.RIME_TC_SPLIT_F16}[args.only])
         fn = lambda: ctx.chi2_async(out)
     elif args.only == "chains":
         # 128 chains, each proposing a move of the brightest source against
@@ -625,7 +625,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the gradient, batched and split-precision comparisons")
-    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "sweep", "chains",
+    ap.add_argument("--only", choices=["chi2", "grad", "batched", "split-bf16", "split-tf32", "split-f16", "sweep", "chains",
                                        "peaks", "fp64"],
                     help="time one form on --workload (optionally with fewer timesteps / channels) "
                          "instead of the benchmark; for profiling")

@@ -186,7 +186,9 @@ rime_status rime_sync(rime_ctx *ctx);
 typedef enum {
     RIME_TC_OFF = 0,          /* direct FP32 source sum (default) */
     RIME_TC_SPLIT_BF16 = 1,   /* tcgen05 products of BF16 hi + lo operand pairs, FP32 accumulation */
-    RIME_TC_SPLIT_TF32 = 2    /* the same with TF32 hi + lo pairs (more accurate, half the rate) */
+    RIME_TC_SPLIT_TF32 = 2,   /* the same with TF32 hi + lo pairs (more accurate, half the rate) */
+    RIME_TC_SPLIT_F16 = 3     /* FP16 hi + lo pairs: TF32's significand at the BF16 rate; scaled
+                                 Stokes values must stay below 6e4 in magnitude */
 } rime_tc_mode;
 
 /* Selects how rime_predict, rime_chi2 and rime_chi2_async evaluate the source
@@ -203,7 +205,11 @@ typedef enum {
  * residuals at a 0.01 Jy noise level; 192 sampled visibilities, chi^2 on one
  * timestep and two channels): BF16 5.7e-6 of the largest visibility and
  * 7.3e-4 of chi^2 (above an FP32 bound of 1e-4); TF32 1.2e-6 and 2.6e-5
- * (within it).
+ * (within it); FP16 8.2e-7 and 2.1e-5 (within it, at the BF16 rate). The
+ * FP16 split needs every scaled Stokes value (the source's Stokes vector
+ * times (nu / nu_ref)^alpha, and E^2 without pointing errors) below 6e4 in
+ * magnitude: otherwise the next waiting call returns RIME_E_INVALID and
+ * leaves its outputs untouched.
  * The split modes take point sources only: a sky model with a Gaussian
  * source makes the next waiting call return RIME_E_INVALID. rime_chi2_grad
  * and rime_chi2_batched always use the direct FP32 path.

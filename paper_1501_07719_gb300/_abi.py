@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "librime.so")
 
 RIME_OK, RIME_E_INVALID, RIME_E_STATE, RIME_E_OOM, RIME_E_CUDA, RIME_E_TIMEOUT, RIME_E_NONFINITE = range(7)
 RIME_FP32, RIME_FP64 = 0, 1
-RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 = 0, 1, 2
+RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32, RIME_TC_SPLIT_F16 = 0, 1, 2, 3
 RIME_KERNEL_AUTO, RIME_KERNEL_TILED, RIME_KERNEL_NARROW = 0, 1, 2
 RIME_BEAM_COS3, RIME_BEAM_JINC = 0, 1
 RIME_PIPE_FFMA, RIME_PIPE_FFMA2, RIME_PIPE_DFMA, RIME_PIPE_EX2 = 0, 1, 2, 3
@@ -363,7 +363,7 @@ def rime_set_kernel(ctx, kernel: int):
 
 
 def rime_set_tensor_mode(ctx, mode: int):
-    """RIME_TC_OFF, RIME_TC_SPLIT_BF16 or RIME_TC_SPLIT_TF32 (FP32 contexts)."""
+    """RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 or RIME_TC_SPLIT_F16 (FP32 contexts)."""
     _check(lib().rime_set_tensor_mode(ctx, int(mode)), ctx)
 
 

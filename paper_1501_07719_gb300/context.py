@@ -95,7 +95,7 @@ class Rime:
 
     def set_tensor_mode(self, mode: int):
         """Tensor-core split-precision source sum for point sources
-        (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32) or the direct sum (RIME_TC_OFF)."""
+        (RIME_TC_SPLIT_BF16 / RIME_TC_SPLIT_TF32 / RIME_TC_SPLIT_F16) or the direct sum (RIME_TC_OFF)."""
         A.rime_set_tensor_mode(self.ctx, mode)
 
     def chains_init(self, nchains: int):

@@ -151,9 +151,15 @@ rime_status sync_status(rime_ctx *c) {
             return fail(c, RIME_E_TIMEOUT, "a kernel gave up a bounded wait (pipeline stalled)");
         }
         if (cls == EC_MODE) {
-            std::snprintf(buf, sizeof buf,
-                          "the split-precision tensor-core mode takes point sources only "
-                          "(first Gaussian source: %lld); use RIME_TC_OFF", idx);
+            if (e & EB_F16)
+                std::snprintf(buf, sizeof buf,
+                              "the FP16 split mode takes scaled Stokes values of magnitude up to 6e4 "
+                              "(first source beyond: %lld); use RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 or RIME_TC_OFF",
+                              idx);
+            else
+                std::snprintf(buf, sizeof buf,
+                              "the split-precision tensor-core mode takes point sources only "
+                              "(first Gaussian source: %lld); use RIME_TC_OFF", idx);
             return fail(c, RIME_E_INVALID, buf);
         }
         if (e & EB_NONFINITE) {
@@ -435,8 +441,9 @@ rime_status rime_chi2_async(rime_ctx *c, double *chi2_dev) {
 
 rime_status rime_set_tensor_mode(rime_ctx *c, int32_t mode) {
     if (!c) return fail(nullptr, RIME_E_INVALID, "ctx is NULL");
-    if (mode != RIME_TC_OFF && mode != RIME_TC_SPLIT_BF16 && mode != RIME_TC_SPLIT_TF32)
-        return fail(c, RIME_E_INVALID, "mode must be RIME_TC_OFF, RIME_TC_SPLIT_BF16 or RIME_TC_SPLIT_TF32");
+    if (mode != RIME_TC_OFF && mode != RIME_TC_SPLIT_BF16 && mode != RIME_TC_SPLIT_TF32 && mode != RIME_TC_SPLIT_F16)
+        return fail(c, RIME_E_INVALID,
+                    "mode must be RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 or RIME_TC_SPLIT_F16");
     if (mode != RIME_TC_OFF && c->dims.precision != RIME_FP32)
         return fail(c, RIME_E_INVALID, "the tensor-core modes need an RIME_FP32 context");
     c->tc_mode = mode;

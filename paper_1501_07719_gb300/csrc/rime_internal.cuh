@@ -45,6 +45,7 @@ enum ErrBits : int {
     EB_NONFINITE = 1,
     EB_RANGE = 2,       // value outside its domain (l^2+m^2 >= 1, w < 0, nu <= 0, axes)
     EB_TIMEOUT = 4,     // a bounded wait inside a kernel gave up
+    EB_F16 = 8,         // EC_MODE: a scaled Stokes value beyond the FP16 split mode's range
 };
 
 // Status block in device memory, copied to the host in one transfer.

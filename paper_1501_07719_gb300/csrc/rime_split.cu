@@ -142,6 +142,41 @@ __device__ __forceinline__ void split_bf16_rot(float x, float y, uint32_t &hi, u
     lo = pack_bf16(dx, dy);
     lr = pack_bf16(-dy, dx);
 }
+// FP16 pairs: the same split as BF16 with the FP16 rounding (11 significant
+// bits, as TF32, and the 16-bit operands of BF16); hi is unpacked by
+// conversion. A remainder below 2^-14 is an FP16 subnormal (absolute
+// spacing 2^-24): a value of magnitude below 1/8 then keeps an absolute error
+// of at most 2^-25 instead of a relative one, which the sums, scaled by
+// |A| <= 1 or the source's flux, tolerate.
+__device__ __forceinline__ uint32_t pack_f16(float x, float y) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(y), "f"(x));
+    return r;
+}
+__device__ __forceinline__ void unpack_f16(uint32_t w, float &x, float &y) {
+    asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(x), "=f"(y)
+        : "r"(w));
+}
+__device__ __forceinline__ void split_f16(float x, float y, uint32_t &hi, uint32_t &lo) {
+    hi = pack_f16(x, y);
+    float xh, yh;
+    unpack_f16(hi, xh, yh);
+    lo = pack_f16(__fsub_rn(x, xh), __fsub_rn(y, yh));
+}
+__device__ __forceinline__ void split_f16_rot(float x, float y, uint32_t &hi, uint32_t &lo, uint32_t &hr,
+                                              uint32_t &lr) {
+    hi = pack_f16(x, y);
+    hr = pack_f16(-y, x);
+    float xh, yh;
+    unpack_f16(hi, xh, yh);
+    const float dx = __fsub_rn(x, xh), dy = __fsub_rn(y, yh);
+    lo = pack_f16(dx, dy);
+    lr = pack_f16(-dy, dx);
+}
+// Operand formats of the split modes.
+enum : int { FMT_BF16 = 0, FMT_TF32 = 1, FMT_F16 = 2 };
+
 // TF32: round to nearest (ties away) into the 19 bits the tensor core reads.
 __device__ __forceinline__ uint32_t tf32_bits(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
@@ -207,8 +242,9 @@ __device__ __forceinline__ bool wait_slot(const Cta &C, int it, int lane, Drain 
 
 // Warps 0-7: A = E K rows (row p, chunk), the drains into register sums, and
 // the epilogue. Returns this thread's chi^2 contribution.
-template <bool TF32, bool WRITE>
+template <int FMT, bool WRITE>
 __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int lane) {
+    constexpr bool TF32 = FMT == FMT_TF32;
     constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
     const SplitParams &P = C.P;
     const int row = tid & 127, chunk = tid >> 7;
@@ -285,7 +321,10 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < SPC; j++) split_bf16(a[j].x, a[j].y, h[j], l[j]);
+            for (int j = 0; j < SPC; j++) {
+                if (FMT == FMT_F16) split_f16(a[j].x, a[j].y, h[j], l[j]);
+                else split_bf16(a[j].x, a[j].y, h[j], l[j]);
+            }
         }
         st16(stg + o_row, h[0], h[1], h[2], h[3]);
         st16(stg + A_BYTES + o_row, l[0], l[1], l[2], l[3]);
@@ -392,8 +431,9 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
 
 // Warps 8-11: B rows (antenna q, chunk, Stokes pair xp): X A_q and i X A_q
 // for X = 2 xp, 2 xp + 1, from one phase per (q, source).
-template <bool TF32>
+template <int FMT>
 __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
+    constexpr bool TF32 = FMT == FMT_TF32;
     constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
     const SplitParams &P = C.P;
     const int bw = warp - NDRAIN / 32;
@@ -446,6 +486,8 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
                 if (TF32) {
                     split_tf32(X * a[j].x, h[2 * j], l[2 * j]);
                     split_tf32(X * a[j].y, h[2 * j + 1], l[2 * j + 1]);
+                } else if (FMT == FMT_F16) {
+                    split_f16_rot(X * a[j].x, X * a[j].y, h[j], l[j], hr[j], lr[j]);
                 } else {
                     split_bf16_rot(X * a[j].x, X * a[j].y, h[j], l[j], hr[j], lr[j]);
                 }
@@ -482,9 +524,11 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
 
 // Warp 12, one thread: the MMAs of each stage into the current segment's
 // TMEM buffer; commits free the stage and, at a segment's end, the buffer.
-template <bool TF32>
+template <int FMT>
 __device__ __forceinline__ void role_mma(const Cta &C) {
-    const uint32_t idesc = tc::instr_desc(TF32 ? tc::kFmtTF32 : tc::kFmtBF16, PT, NB);
+    constexpr bool TF32 = FMT == FMT_TF32;
+    const uint32_t idesc =
+        tc::instr_desc(TF32 ? tc::kFmtTF32 : FMT == FMT_F16 ? tc::kFmtF16 : tc::kFmtBF16, PT, NB);
     const uint32_t sbase = tc::smem_u32(C.smem);
     for (int it = 0; it < C.nstg; it++) {
         const int g = it / SEG, b = g & 1, first = it % SEG == 0;
@@ -521,8 +565,9 @@ __device__ __forceinline__ void role_mma(const Cta &C) {
     tc::mbar_wait_plain(C.drained, 0, tc::kWaitLimitNs);
 }
 
-template <bool TF32, bool WRITE>
+template <int FMT, bool WRITE>
 __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
+    constexpr bool TF32 = FMT == FMT_TF32;
     constexpr int SPS = Item<TF32>::SPS;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t full[NST], empty[NST], seg_full[2], seg_empty[2], drained;
@@ -564,13 +609,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     double chi = 0.0;
     if (warp < NDRAIN / 32) {
         tc::regs_inc<Regs<TF32>::A>();
-        chi = role_a<TF32, WRITE>(C, tid, warp, lane);
+        chi = role_a<FMT, WRITE>(C, tid, warp, lane);
     } else if (warp < NPROD / 32) {
         tc::regs_dec<Regs<TF32>::B>();
-        role_b<TF32>(C, warp, lane);
+        role_b<FMT>(C, warp, lane);
     } else {
         tc::regs_dec<REGS_MMA>();
-        if (warp == NPROD / 32 && lane == 0) role_mma<TF32>(C);
+        if (warp == NPROD / 32 && lane == 0) role_mma<FMT>(C);
     }
     const uint32_t tmem = tmem_base;
 
@@ -617,8 +662,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
 // times the spectral factor (nu/nu_ref)^alpha (eq. 2) and, without pointing
 // errors, times the beam of both antennas E_s^2 (eq. 4; the same for every
 // antenna). out [trows][nchan][nsrc_pad][4], zero for s >= nsrc.
+// FP16 split: B = X A with |A| <= 1 must stay below the FP16 maximum (65504)
+// with room for the rounding of its high part.
+constexpr float kF16Limit = 6.0e4f;
 __global__ void k_split_scales(int nsrc, int nsrc_pad, int nchan, int trows, int na, const ChanF *chan,
-                               const float *stokes, const float *alpha, const float *rho, int pointing, float4 *out) {
+                               const float *stokes, const float *alpha, const float *rho, int pointing, float4 *out,
+                               int f16, DevStatus *st) {
     const long long n = (long long)trows * nchan * nsrc_pad;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int s = (int)(i % nsrc_pad);
@@ -635,8 +684,13 @@ __global__ void k_split_scales(int nsrc, int nsrc_pad, int nchan, int trows, int
             const float E = beam_f(rho[(long long)s * na], ch);   // timestep 0, any antenna
             f *= E * E;
         }
-        const float4 st = reinterpret_cast<const float4 *>(stokes)[(long long)t * nsrc + s];
-        out[i] = make_float4(st.x * f, st.y * f, st.z * f, st.w * f);
+        const float4 sv = reinterpret_cast<const float4 *>(stokes)[(long long)t * nsrc + s];
+        const float4 o = make_float4(sv.x * f, sv.y * f, sv.z * f, sv.w * f);
+        out[i] = o;
+        if (f16 && !(fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w))) <= kF16Limit)) {
+            atomicOr(&st->err[EC_MODE], EB_F16);
+            atomicMin(&st->first_bad[EC_MODE], (long long)s);
+        }
     }
 }
 
@@ -714,7 +768,8 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
                                                   reinterpret_cast<const float *>(c->d_stokes),
                                                   reinterpret_cast<const float *>(c->d_alpha),
                                                   reinterpret_cast<const float *>(c->d_rho), c->has_pointing,
-                                                  reinterpret_cast<float4 *>(c->d_sscale));
+                                                  reinterpret_cast<float4 *>(c->d_sscale),
+                                                  c->tc_mode == RIME_TC_SPLIT_F16, c->d_status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -756,9 +811,11 @@ cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result)
         kernel<<<(unsigned)blocks, THREADS, SMEM_BYTES, c->stream>>>(P);
         return cudaGetLastError();
     };
-    const bool tf32 = c->tc_mode == RIME_TC_SPLIT_TF32;
-    if (tf32) return write ? go(k_split<true, true>) : go(k_split<true, false>);
-    return write ? go(k_split<false, true>) : go(k_split<false, false>);
+    if (c->tc_mode == RIME_TC_SPLIT_TF32)
+        return write ? go(k_split<FMT_TF32, true>) : go(k_split<FMT_TF32, false>);
+    if (c->tc_mode == RIME_TC_SPLIT_F16)
+        return write ? go(k_split<FMT_F16, true>) : go(k_split<FMT_F16, false>);
+    return write ? go(k_split<FMT_BF16, true>) : go(k_split<FMT_BF16, false>);
 }
 
 }  // namespace rime

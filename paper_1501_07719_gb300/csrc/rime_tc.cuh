@@ -42,9 +42,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 }
 
 // Instruction descriptor of kind::f16 / kind::tf32: D in F32, A and B of the
-// same format (BF16 = 1 for kind::f16, TF32 = 2 for kind::tf32), both
-// K-major, no negation, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-enum : uint32_t { kFmtBF16 = 1, kFmtTF32 = 2 };
+// same format (F16 = 0 or BF16 = 1 for kind::f16, TF32 = 2 for kind::tf32),
+// both K-major, no negation, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+enum : uint32_t { kFmtF16 = 0, kFmtBF16 = 1, kFmtTF32 = 2 };
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, int M, int N) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }

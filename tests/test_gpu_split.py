@@ -22,17 +22,20 @@ pytestmark = pytest.mark.gpu
 # keeps that bias near 1e-6. chi^2 inherits |dV|^2 / |V - D|^2 with V - D at
 # the 0.01 Jy noise level: measured up to 6e-5 (BF16) and 1e-5 (TF32) on these
 # cases.
-VTOL = {"bf16": 3e-5, "tf32": 3e-6}
-CTOL = {"bf16": 3e-4, "tf32": 5e-5}
+# FP16 pairs keep TF32's 11 significant bits (their remainders below 2^-14
+# are subnormal: an absolute 2^-25); measured on these cases up to 6.7e-7
+# (visibilities) and 7.4e-6 (chi^2).
+VTOL = {"bf16": 3e-5, "tf32": 3e-6, "f16": 1e-6}
+CTOL = {"bf16": 3e-4, "tf32": 5e-5, "f16": 1.1e-5}
 # The 256-antenna, 4096-source workload (|V| ~ 1e2 Jy, residuals at the noise
 # level), about 1.5 times the errors measured there (the bench's split form
 # measures the same samples and slice): visibilities over the 192 sampled
-# (t, baseline, channel) below, BF16 5.7e-6, TF32 1.17e-6; chi^2 on timestep 0, channels
-# 0-1 with data = the oracle's model + noise, BF16 7.3e-4, TF32 2.6e-5 (the
-# direct FP32 path 1.2e-5). BF16 does not reach the FP32 chi^2 bound of 1e-4
-# there; TF32 does.
-VTOL_256 = {"bf16": 8.5e-6, "tf32": 1.8e-6}
-CTOL_256 = {"bf16": 1.1e-3, "tf32": 4e-5}
+# (t, baseline, channel) below, BF16 5.7e-6, TF32 1.17e-6, FP16 8.2e-7; chi^2 on timestep 0,
+# channels 0-1 with data = the oracle's model + noise, BF16 7.3e-4, TF32 2.6e-5,
+# FP16 2.1e-5 (the direct FP32 path 1.2e-5). BF16 does not reach the FP32 chi^2
+# bound of 1e-4 there; TF32 and FP16 do.
+VTOL_256 = {"bf16": 8.5e-6, "tf32": 1.8e-6, "f16": 1.2e-6}
+CTOL_256 = {"bf16": 1.1e-3, "tf32": 4e-5, "f16": 3.1e-5}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,7 +47,7 @@ def _cuda():
 
 def _mode(name):
     import paper_1501_07719_gb300 as R
-    return {"bf16": R.RIME_TC_SPLIT_BF16, "tf32": R.RIME_TC_SPLIT_TF32}[name]
+    return {"bf16": R.RIME_TC_SPLIT_BF16, "tf32": R.RIME_TC_SPLIT_TF32, "f16": R.RIME_TC_SPLIT_F16}[name]
 
 
 CASES = {
@@ -62,7 +65,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("split", ["bf16", "tf32"])
+@pytest.mark.parametrize("split", ["bf16", "tf32", "f16"])
 @pytest.mark.parametrize("case", list(CASES))
 def test_split_matches_oracle(case, split):
     inp = make_case(precision="f32", **CASES[case])
@@ -148,6 +151,28 @@ def test_split_rejects_gaussian_sources_and_fp64():
     r.close()
 
 
+def test_f16_split_rejects_stokes_beyond_its_range():
+    """A source whose scaled Stokes vector exceeds the FP16 split's range
+    (6e4 in magnitude) makes the FP16 mode's call return RIME_E_INVALID, its
+    output untouched; the BF16 split takes the same model."""
+    import paper_1501_07719_gb300 as R
+    inp = make_case(rime_synth.custom(9, 2, 2, 3, 0, seed_index=83), "f32")
+    inp["sources"]["stokes"][1] = [2e5, 0.0, 0.0, 0.0]   # at the phase centre: E = 1
+    inp["sources"]["lm"][1] = [0.0, 0.0]
+    want = oracle.Problem(inp, data=inp["data"]).chi2()
+    r = gpu_ctx(inp, "f32")
+    r.set_tensor_mode(R.RIME_TC_SPLIT_F16)
+    out = r.torch.full((1,), 7.0, dtype=r.torch.float64, device="cuda")
+    r.chi2_async(out)
+    with pytest.raises(R.RimeError) as e:
+        r.sync()
+    assert e.value.status == R._abi.RIME_E_INVALID and "FP16" in str(e.value)
+    assert float(out.item()) == 7.0
+    r.set_tensor_mode(R.RIME_TC_SPLIT_BF16)
+    assert rel_err(r.chi2(), want) <= CTOL["bf16"]
+    r.close()
+
+
 def test_split_256ant_slice_chi2_against_oracle():
     """The 256-antenna, 4096-point workload on one timestep and two channels
     (267 M source-terms): chi^2 of both splits and of the direct path against
@@ -167,14 +192,14 @@ def test_split_256ant_slice_chi2_against_oracle():
     # the FP32 bound. The TF32 split adds short MMA segments into its running
     # sums too. The BF16 split's |dV| (~4e-6 of max |V|) shows at ~1e-3.
     for mode, tol in ((R.RIME_TC_OFF, 1e-4), (R.RIME_TC_SPLIT_BF16, CTOL_256["bf16"]),
-                      (R.RIME_TC_SPLIT_TF32, CTOL_256["tf32"])):
+                      (R.RIME_TC_SPLIT_TF32, CTOL_256["tf32"]), (R.RIME_TC_SPLIT_F16, CTOL_256["f16"])):
         r.set_tensor_mode(mode)
         got = r.chi2()
         assert rel_err(got, want) <= tol, (mode, got, want)
     r.close()
 
 
-@pytest.mark.parametrize("split", ["bf16", "tf32"])
+@pytest.mark.parametrize("split", ["bf16", "tf32", "f16"])
 def test_split_full_256ant_sampled(split):
     """The 256-antenna, 20-timestep, 128-channel, 4096-point workload in the
     benchmark's configuration: sampled visibilities against the oracle."""
@@ -222,7 +247,7 @@ def test_phase_argument_matches_fp64_reduction():
     assert np.all(d <= bound), float((d / bound).max())
 
 
-@pytest.mark.parametrize("split", ["bf16", "tf32"])
+@pytest.mark.parametrize("split", ["bf16", "tf32", "f16"])
 def test_bounded_wait_gives_up_and_the_next_call_recovers(split):
     """With a 1 ns wait limit, the first wait of the tensor-core pipeline that
     is not already satisfied gives up: the block records the timeout, waits
