@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     const int beam_model = GENERAL ? reinterpret_cast<const ChanF *>(P.chan)[0].beam : RIME_BEAM_COS3;
     using T = float;
     using T2 = float2;
-    constexpr int SG = GCfg<float>::SG, NP = SG / 2, NG = GTHREADS / NP;
+    constexpr int SG = GCfg<float>::SG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *rTau = reinterpret_cast<float2 *>(smem_raw);
     T *rRho = reinterpret_cast<T *>(rTau + SG * GNLOC);
@@ -400,9 +400,17 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
 
     if (inputs_bad(P.status)) return;
     const int tid = threadIdx.x;
-    const int sp = tid % NP, grp = tid / NP;
     int bid = blockIdx.x;
     const int sch = bid % P.nsch;
+    // NP source pairs x NG baseline groups: a chunk with fewer than SG
+    // sources (the list's last) gives its threads more baseline groups
+    // rather than idle duplicate sources (NP the power of two that covers its
+    // pairs, NP NG = GTHREADS)
+    const int npair = (min(SG, P.nsrc - sch * SG) + 1) / 2;
+    int NP = SG / 2;
+    while (NP / 2 >= npair) NP /= 2;
+    const int NG = GTHREADS / NP;
+    const int sp = tid % NP, grp = tid / NP;
     bid /= P.nsch;
     const int u = bid % P.nunits;
     bid /= P.nunits;
@@ -414,8 +422,9 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     const bool pointing = P.has_pointing != 0;
     const int k0 = cg * P.chan_group, k1 = min(P.nchan, k0 + P.chan_group);
 
-    for (int i = tid; i < nloc * SG; i += GTHREADS) {
-        const int a = i / SG, ss = i - a * SG;
+    const int nss = 2 * NP;   // source slots the threads read (the rest are never staged)
+    for (int j = tid; j < nloc * nss; j += GTHREADS) {
+        const int a = j / nss, ss = j - a * nss, i = a * SG + ss;
         const int src = min(sch * SG + ss, P.nsrc - 1);
         const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
         const long long di = ((long long)t * P.nsrc + src) * P.na + ant;
@@ -489,7 +498,8 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
     for (int k = k0; k < k1; k++) {
         const ChanF ch = reinterpret_cast<const ChanF *>(P.chan)[k];
         __syncthreads();
-        for (int i = tid; i < nloc * SG; i += GTHREADS) {
+        for (int j = tid; j < nloc * nss; j += GTHREADS) {
+            const int i = (j / nss) * SG + (j % nss);
             T2 v = f32::phase_factor(rTau[i], ch);   // the forward kernels' K
             if (pointing) {
                 const int a = i / SG, ss = i - a * SG;
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
 #pragma unroll
     for (int h = 0; h < 2; h++)
 #pragma unroll
-        for (int i = 0; i < NGRAD; i++) sRed[(grp * SG + 2 * sp + h) * NGRAD + i] = out[h][i];
+        for (int i = 0; i < NGRAD; i++) sRed[(grp * 2 * NP + 2 * sp + h) * NGRAD + i] = out[h][i];
     __syncthreads();
     if (grp == 0) {
 #pragma unroll
@@ -654,7 +664,7 @@ __global__ void __launch_bounds__(GTHREADS, 2) k_grad_src_f32x2(const GradParams
             double *o = P.partials + (prow * P.nsrc + sidx[h]) * NGRAD;
             for (int i = 0; i < NGRAD; i++) {
                 double v = 0.0;
-                for (int g = 0; g < NG; g++) v += sRed[(g * SG + 2 * sp + h) * NGRAD + i];
+                for (int g = 0; g < NG; g++) v += sRed[(g * 2 * NP + 2 * sp + h) * NGRAD + i];
                 o[i] = v;
             }
         }
