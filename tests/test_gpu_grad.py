@@ -45,6 +45,9 @@ CASES = {
                                  pointing_sigma=0.003),
     # 500 sources: the FP32 forward pass folds segments of its source sum
     "36ant-long-list": dict(wl=rime_synth.custom(36, 1, 2, 250, 250, seed_index=62)),
+    # 33 sources: the FP32 source pass's second chunk holds one source (one
+    # source pair, 256 baseline groups)
+    "30ant-33src": dict(wl=rime_synth.custom(30, 2, 2, 17, 16, seed_index=63)),
 }
 
 
