@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     using T2 = typename C::T2;
     using Chan = typename C::Chan;
     using TauT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
-    constexpr int SG = C::SG, NG = GTHREADS / SG;
+    constexpr int SG = C::SG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // layout: raw tau | raw rho | A | [dlnE] | baseline table | Y chunk
     TauT *rTau = reinterpret_cast<TauT *>(smem_raw);
@@ -155,9 +155,16 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
 
     if (inputs_bad(P.status)) return;
     const int tid = threadIdx.x;
-    const int sl = tid % SG, grp = tid / SG;
     int bid = blockIdx.x;
     const int sch = bid % P.nsch;
+    // NS sources x NG baseline groups: a chunk with fewer than SG sources (the
+    // list's last) gives its threads more baseline groups rather than idle
+    // duplicate sources (NS the power of two that covers them, NS NG = GTHREADS)
+    const int nact = min(SG, P.nsrc - sch * SG);
+    int NS = SG;
+    while (NS / 2 >= nact) NS /= 2;
+    const int NG = GTHREADS / NS;
+    const int sl = tid % NS, grp = tid / NS;
     bid /= P.nsch;
     const int u = bid % P.nunits;
     bid /= P.nunits;
@@ -173,8 +180,8 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     const int k0 = cg * P.chan_group, k1 = min(P.nchan, k0 + P.chan_group);
 
     // ---- per block: delays of every (antenna, source) and the baseline table ----
-    for (int i = tid; i < nloc * SG; i += GTHREADS) {
-        const int a = i / SG, ss = i - a * SG;
+    for (int j = tid; j < nloc * NS; j += GTHREADS) {   // the source slots the threads read
+        const int a = j / NS, ss = j - a * NS, i = a * SG + ss;
         const int src = min(sch * SG + ss, P.nsrc - 1);
         const int ant = a < U.nr ? U.r0 + a : U.c0 + (a - U.nr);
         const long long di = ((long long)t * P.nsrc + src) * P.na + ant;
@@ -241,7 +248,8 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
         const Chan ch = reinterpret_cast<const Chan *>(P.chan)[k];
         __syncthreads();   // delays staged / the previous channel is done with sA
         // ---- A (= K, or E K with pointing errors) of every (antenna, source) ----
-        for (int i = tid; i < nloc * SG; i += GTHREADS) {
+        for (int j = tid; j < nloc * NS; j += GTHREADS) {
+            const int i = (j / NS) * SG + (j % NS);
             T2 v = phase(rTau + i, 0, ch);
             if (pointing) {
                 const int a = i / SG, ss = i - a * SG;
@@ -357,14 +365,14 @@ __global__ void __launch_bounds__(GTHREADS) k_grad_src(const GradParams P) {
     // ---- combine the baseline groups in a fixed order: one partial per source ----
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < NGRAD; i++) sRed[(grp * SG + sl) * NGRAD + i] = out[i];
+    for (int i = 0; i < NGRAD; i++) sRed[(grp * NS + sl) * NGRAD + i] = out[i];
     __syncthreads();
     if (grp == 0 && sact) {
         const long long prow = ((long long)t * P.ncg + cg) * P.nunits + u;
         double *o = P.partials + (prow * P.nsrc + s) * NGRAD;
         for (int i = 0; i < NGRAD; i++) {
             double v = 0.0;
-            for (int g = 0; g < NG; g++) v += sRed[(g * SG + sl) * NGRAD + i];
+            for (int g = 0; g < NG; g++) v += sRed[(g * NS + sl) * NGRAD + i];
             o[i] = v;
         }
     }
