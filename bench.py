@@ -575,6 +575,7 @@ def run_only(args):
         fn()
     torch.cuda.synchronize()
     ms = _timed(torch, stream, fn, args.steps)
+    ctx.sync()   # a deferred error (e.g. a split mode given Gaussian sources) raises here
     ctx.close()
     print(json.dumps({"only": args.only, "workload": wl.name, "ntime": wl.ntime, "nchan": wl.nchan,
                       "median_ms": ms}), flush=True)

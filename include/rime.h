@@ -203,9 +203,9 @@ typedef enum {
  * rime_phase_turns), and the chi^2 is summed in FP64. Errors against the FP64
  * result on 256 antennas, 128 channels and 4096 point sources (|V| ~ 1e2 Jy,
  * residuals at a 0.01 Jy noise level; 192 sampled visibilities, chi^2 on one
- * timestep and two channels): BF16 5.7e-6 of the largest visibility and
- * 7.3e-4 of chi^2 (above an FP32 bound of 1e-4); TF32 1.2e-6 and 2.6e-5
- * (within it); FP16 8.2e-7 and 2.1e-5 (within it, at the BF16 rate). The
+ * timestep and two channels): BF16 5.8e-6 of the largest visibility and
+ * 7.7e-4 of chi^2 (above an FP32 bound of 1e-4); TF32 8.6e-7 and 3.0e-5
+ * (within it); FP16 8.7e-7 and 1.7e-5 (within it, at the BF16 rate). The
  * FP16 split needs every scaled Stokes value (the source's Stokes vector
  * times (nu / nu_ref)^alpha, and E^2 without pointing errors) below 6e4 in
  * magnitude: otherwise the next waiting call returns RIME_E_INVALID and
@@ -215,6 +215,20 @@ typedef enum {
  * and rime_chi2_batched always use the direct FP32 path.
  *   mode  a rime_tc_mode; RIME_E_INVALID for an RIME_FP64 context. */
 rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
+
+/* The split modes' tile plan for na antennas (host only, no GPU needed).
+ * Antennas fall into groups of 32 (the last one ragged); one CTA of the split
+ * kernel computes, for one (t, k), the products of up to four row groups
+ * (128 rows) against one column group. S_X is Hermitian (S_X[q, p] =
+ * conj S_X[p, q] for real X), so each unordered pair of distinct groups is
+ * computed in exactly one tile, in either orientation, and each group's own
+ * baselines in one tile whose rows include the column group itself.
+ *   na    antennas, 2 .. 4096
+ *   out   [cap][5] int32: the column group, then four row groups (-1: empty)
+ *   cap   tiles out can hold (0: only count them)
+ * Returns the number of tiles (256 antennas: 9), or -1 for na out of range,
+ * cap < 0, or out NULL with cap > 0. */
+int32_t rime_split_tiles(int32_t na, int32_t *out, int32_t cap);
 
 /* chi^2 (eq. 7, without the ln-weight term) of an observation whose data
  * and weights stay in host memory, streamed to the GPU in chunks of

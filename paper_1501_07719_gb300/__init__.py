@@ -9,7 +9,7 @@ from ._abi import (RIME_BEAM_COS3, RIME_BEAM_JINC, RIME_PIPE_DFMA, RIME_PIPE_EX2
                    rime_chi2_noalloc, rime_chi2_streamed, rime_create, rime_destroy, rime_last_error, rime_ln_norm, rime_nbl,
                    rime_predict, rime_set_batched_config, rime_set_data, rime_set_gains, rime_set_sources,
                    rime_set_beam, rime_set_kernel, rime_set_tensor_mode, rime_set_uvw, rime_set_wait_limit, rime_sync,
-                   rime_phase_turns, rime_pipe_rate)
+                   rime_phase_turns, rime_pipe_rate, rime_split_tiles)
 from .context import Rime
 from .autograd import RimeChi2
 
@@ -19,4 +19,5 @@ __all__ = ["RIME_BEAM_COS3", "RIME_BEAM_JINC", "RIME_PIPE_DFMA", "RIME_PIPE_EX2"
            "rime_chi2_grad", "rime_chi2_noalloc", "rime_chi2_streamed", "rime_create", "rime_destroy", "rime_last_error", "rime_ln_norm",
            "rime_nbl", "rime_predict", "rime_set_batched_config", "rime_set_data", "rime_set_gains",
            "rime_set_beam", "rime_set_kernel", "rime_set_sources", "rime_set_tensor_mode", "rime_set_uvw",
-           "rime_set_wait_limit", "rime_sync", "rime_phase_turns", "rime_pipe_rate"]
+           "rime_set_wait_limit", "rime_sync", "rime_phase_turns", "rime_pipe_rate",
+           "rime_split_tiles"]

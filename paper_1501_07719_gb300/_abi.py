@@ -78,6 +78,7 @@ def lib():
         L.rime_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_batched_config.argtypes = [vp, C.POINTER(rime_batch_config)]
         L.rime_set_tensor_mode.argtypes = [vp, C.c_int32]
+        L.rime_split_tiles.argtypes, L.rime_split_tiles.restype = [C.c_int32, vp, C.c_int32], C.c_int32
         L.rime_set_kernel.argtypes = [vp, C.c_int32]
         L.rime_set_wait_limit.argtypes, L.rime_set_wait_limit.restype = [vp, C.c_uint64], ip
         L.rime_set_beam.argtypes = [vp, C.c_int32, C.c_double]
@@ -365,6 +366,16 @@ def rime_set_kernel(ctx, kernel: int):
 def rime_set_tensor_mode(ctx, mode: int):
     """RIME_TC_OFF, RIME_TC_SPLIT_BF16, RIME_TC_SPLIT_TF32 or RIME_TC_SPLIT_F16 (FP32 contexts)."""
     _check(lib().rime_set_tensor_mode(ctx, int(mode)), ctx)
+
+
+def rime_split_tiles(na: int) -> np.ndarray:
+    """The split modes' tile plan: [ntiles, 5] int32 rows (column group, four row groups, -1 empty)."""
+    n = lib().rime_split_tiles(int(na), None, 0)
+    if n < 0:
+        raise RimeError(RIME_E_INVALID, f"rime_split_tiles: na = {na} out of range")
+    out = np.zeros((n, 5), dtype=np.int32)
+    lib().rime_split_tiles(int(na), out.ctypes.data_as(C.c_void_p), n)
+    return out
 
 
 def rime_phase_turns(nu_hz, tau_s) -> np.ndarray:

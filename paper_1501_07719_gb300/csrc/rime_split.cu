@@ -21,7 +21,8 @@
 // is dropped.
 //
 // One CTA owns (t, k) and a tile of 128 row antennas p (the MMA's M, one
-// TMEM lane each) by 32 column antennas q; the B operand has one row per
+// TMEM lane each: four groups of 32 antennas, see split_tiles) by a group of
+// 32 column antennas q; the B operand has one row per
 // (q, X) for the real parts and one per (q, X) for the imaginary parts,
 // N = 256, so one MMA reads A once for both. Twelve producer warps form the
 // operands of each chunk of
@@ -94,7 +95,7 @@ struct SplitParams {
     int na, ntime, nchan, nsrc, ntiles;
     long long nbl;
     int has_gains, has_weight, has_pointing;
-    const int2 *tiles;        // (p0, q0) of each tile
+    const int2 *tiles;        // (column group, packed row groups) of each tile (split_tiles)
     const ChanF *chan;
     const float2 *tau;        // [ntime][nsrc][na] double-float delays (s)
     const float *rho;         // [ntime][nsrc][na] beam radii
@@ -209,7 +210,8 @@ struct Cta {
     uint64_t *full, *empty, *seg_full, *seg_empty, *drained;
     int *abort_flag;
     uint32_t tmem;
-    int t, k, p0, q0, nstg, nseg;
+    int t, k, cg, nstg, nseg;
+    uint32_t rows;   // row groups of the tile: 8 bits per 32-row slot, 0xff empty
     ChanF ch;
 };
 
@@ -248,7 +250,8 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
     constexpr int SPC = Item<TF32>::SPC, SPS = Item<TF32>::SPS;
     const SplitParams &P = C.P;
     const int row = tid & 127, chunk = tid >> 7;
-    const int ant = min(C.p0 + row, P.na - 1);
+    const int rgrp = (C.rows >> (8 * (row >> 5))) & 0xff;   // 0xff: an empty slot, formed from antenna 0
+    const int ant = rgrp == 0xff ? 0 : min(QT * rgrp + (row & 31), P.na - 1);
     const long long tbase = (long long)C.t * P.nsrc * P.na + ant;
     const uint32_t o_row = tc::operand_offset(row, 16 * chunk);
     const bool pointing = P.has_pointing != 0;
@@ -358,7 +361,7 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         return 0.0;
     }
 
-    // ---- epilogue: row p = lrow against q = 16 half .. 16 half + 15 ----
+    // ---- epilogue: row lrow (antenna p) against columns q = 16 half .. 16 half + 15 of the column group ----
     // Every MMA has completed and every stage has been consumed, so the stage
     // buffers take this thread's sums ([256 columns][128 rows]); each thread
     // reads back only what it wrote.
@@ -369,8 +372,11 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         ts[(128 + 64 * half + c) * 128 + lrow] = tot[64 + c];
     }
     double chi = 0.0;
-    const int pgl = C.p0 + lrow;
-    const bool prow = pgl < P.na;
+    const int rg = (C.rows >> (8 * quad)) & 0xff;   // the row group of slot quad
+    const int pgl = QT * rg + lane;
+    const bool prow = rg != 0xff && pgl < P.na;
+    const bool same = rg == C.cg;   // pairs inside one group: p < q only
+    const bool swap = rg > C.cg;    // p > q for the whole slot: the tile holds S_X[p, q] = conj S_X[q, p]
     const int t = C.t, k = C.k;
     float2 gp[4] = {{1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
     if (P.has_gains && prow) {
@@ -379,16 +385,16 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
         gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
     }
-    const long long rowbase = (long long)pgl * P.na - (long long)pgl * (pgl + 1) / 2 - pgl - 1;
 #pragma unroll 1
     for (int i = 0; i < 16; i++) {
-        const int q = C.q0 + 16 * half + i;
-        if (!(prow && pgl < q && q < P.na)) continue;
+        const int q = QT * C.cg + 16 * half + i;
+        if (!(prow && q < P.na && (!same || pgl < q))) continue;
         float Sv[8];   // Re I, Q, U, V then Im I, Q, U, V
 #pragma unroll
         for (int x = 0; x < 4; x++) {
             Sv[x] = ts[(64 * half + 4 * i + x) * 128 + lrow];
             Sv[4 + x] = ts[(128 + 64 * half + 4 * i + x) * 128 + lrow];
+            if (swap) Sv[4 + x] = -Sv[4 + x];   // baseline (q, p): S_X[q, p]
         }
         float2 Sm[4];
         Sm[0] = make_float2(Sv[0] + Sv[1], Sv[4] + Sv[5]);   // I + Q
@@ -402,11 +408,13 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
             gq[0] = make_float2(b01.x, b01.y); gq[1] = make_float2(b01.z, b01.w);
             gq[2] = make_float2(b23.x, b23.y); gq[3] = make_float2(b23.z, b23.w);
         }
-        float2 V[4], tmp[4], gqh[4];
-        mmul(gp, Sm, tmp);   // eq. 1: V = G_p S G_q^H
-        mherm(gq, gqh);
-        mmul(tmp, gqh, V);
-        const long long vrow = ((long long)t * P.nbl + rowbase + q) * P.nchan + k;
+        float2 V[4], tmp[4], gbh[4];
+        // eq. 1 for the baseline (a, b), a < b: V = G_a S G_b^H
+        mmul(swap ? gq : gp, Sm, tmp);
+        mherm(swap ? gp : gq, gbh);
+        mmul(tmp, gbh, V);
+        const long long a = swap ? q : pgl, b = swap ? pgl : q;
+        const long long vrow = ((long long)t * P.nbl + a * P.na - a * (a + 1) / 2 - a - 1 + b) * P.nchan + k;
         if (WRITE) {
             float4 *o = reinterpret_cast<float4 *>(P.vis_out + 4 * vrow);
             o[0] = make_float4(V[0].x, V[0].y, V[1].x, V[1].y);
@@ -439,7 +447,7 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
     const int bw = warp - NDRAIN / 32;
     const int chunk = bw & 1, xp = bw >> 1;
     const int row = lane;
-    const int ant = min(C.q0 + row, P.na - 1);
+    const int ant = min(QT * C.cg + row, P.na - 1);
     const long long tbase = (long long)C.t * P.nsrc * P.na + ant;
     const float2 *scale = reinterpret_cast<const float2 *>(P.scale) +
                           2 * ((long long)(P.scale_trows > 1 ? C.t : 0) * P.nchan * P.nsrc_pad + (long long)C.k * P.nsrc_pad);
@@ -581,7 +589,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     const int rest = blockIdx.x / P.ntiles;
     const int k = rest % P.nchan;
     const int t = rest / P.nchan;
-    const int2 pq = P.tiles[tile];
+    const int2 tl = P.tiles[tile];
     const int nstg = (P.nsrc + SPS - 1) / SPS;
 
     if (tid == 0) {
@@ -604,8 +612,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_split(const SplitParams P) {
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    const Cta C{P, smem, full, empty, seg_full, seg_empty, &drained, &abort_flag, tmem_base, t, k, pq.x, pq.y,
-                nstg, (nstg + SEG - 1) / SEG, P.chan[k]};
+    const Cta C{P, smem, full, empty, seg_full, seg_empty, &drained, &abort_flag, tmem_base, t, k, tl.x, nstg,
+                (nstg + SEG - 1) / SEG, (uint32_t)tl.y, P.chan[k]};
     double chi = 0.0;
     if (warp < NDRAIN / 32) {
         tc::regs_inc<Regs<TF32>::A>();
@@ -705,13 +713,102 @@ __global__ void k_check_points(int nsrc, const float *gauss, DevStatus *st) {
 
 }  // namespace split
 
-// Tiles (p0, q0) with at least one pair p < q inside the array.
+// Tile plan. Antennas fall into groups of QT = 32 (the last one ragged); a
+// tile pairs one column group c (the MMA's N side) with up to four row groups
+// (its M = 128 rows). S_X is Hermitian for real X (S_X[q, p] = conj S_X[p, q]),
+// so each unordered pair of distinct groups {a, b} is computed once, as rows
+// of a against column group b or the reverse, in the tiles of the group that
+// owns the pair, and each group's own pairs p < q in one tile whose rows
+// include the column group itself. Group c with o_c owned pairs needs
+// ceil((o_c + 1) / 4) tiles. Each group is given a budget of t_c tiles, so at
+// most 4 t_c - 1 owned pairs: the pairs can be shared out within the budgets
+// iff every set of k groups can hold the k (k - 1) / 2 pairs among them, and
+// the k groups of smallest budget are the tightest set; the budgets start at
+// one tile and the smallest is raised until that holds. The pairs are then
+// shared out along augmenting paths (a full group passes one of its pairs
+// on to the pair's other group). 256 antennas (8 groups): 9 tiles, against
+// the 12 of a plan of 128-antenna row blocks against 32-antenna column blocks,
+// whose tiles on the diagonal hold half as many baselines.
+// Tile encoding: x = c, y = row groups (8 bits each, slot 0 lowest, 0xff empty).
 std::vector<int2> split_tiles(int na) {
-    std::vector<int2> v;
-    for (int p0 = 0; p0 < na; p0 += split::PT)
-        for (int q0 = 0; q0 < na; q0 += split::QT)
-            if (p0 < std::min(na, q0 + split::QT) - 1) v.push_back(make_int2(p0, q0));
-    return v;
+    using split::QT;
+    std::vector<int2> out;
+    if (na < 2) return out;
+    const int G = (na + QT - 1) / QT;
+    std::vector<int> budget(G, 1), idx(G);
+    for (;;) {
+        for (int c = 0; c < G; c++) idx[c] = c;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return budget[a] < budget[b]; });
+        long long held = 0;
+        bool ok = true;
+        for (int k = 1; k <= G && ok; k++) {
+            held += 4 * budget[idx[k - 1]] - 1;
+            ok = held >= (long long)k * (k - 1) / 2;
+        }
+        if (ok) break;
+        budget[idx[0]]++;
+    }
+    // own[a * G + b]: group a owns the pair {a, b}
+    std::vector<char> own((size_t)G * G, 0);
+    std::vector<int> nown(G, 0), from(G);
+    auto spare = [&](int v) { return nown[v] < 4 * budget[v] - 1; };
+    for (int a = 0; a < G; a++)
+        for (int b = a + 1; b < G; b++) {
+            const int first = nown[a] - 4 * budget[a] <= nown[b] - 4 * budget[b] ? a : b, second = a + b - first;
+            if (spare(first) || spare(second)) {
+                const int v = spare(first) ? first : second;
+                own[(size_t)v * G + (a + b - v)] = 1;
+                nown[v]++;
+                continue;
+            }
+            // breadth-first search from a and b over "v passes a pair {v, w} to w"
+            std::fill(from.begin(), from.end(), -2);
+            std::vector<int> queue{a, b};
+            from[a] = from[b] = -1;
+            int end = -1;
+            for (size_t h = 0; h < queue.size() && end < 0; h++) {
+                const int v = queue[h];
+                for (int w = 0; w < G && end < 0; w++)
+                    if (own[(size_t)v * G + w] && from[w] == -2) {
+                        from[w] = v;
+                        if (spare(w)) end = w;
+                        else queue.push_back(w);
+                    }
+            }
+            if (end < 0) return {};   // cannot happen once the budgets pass the test above
+            nown[end]++;
+            int w = end;
+            for (; from[w] >= 0; w = from[w]) {   // move {from[w], w} to w along the path
+                own[(size_t)from[w] * G + w] = 0;
+                own[(size_t)w * G + from[w]] = 1;
+            }
+            own[(size_t)w * G + (a + b - w)] = 1;   // the path's start takes the new pair
+        }
+    for (int c = 0; c < G; c++) {
+        std::vector<int> rows{c};
+        for (int w = 0; w < G; w++)
+            if (own[(size_t)c * G + w]) rows.push_back(w);
+        for (size_t i = 0; i < rows.size(); i += 4) {
+            uint32_t packed = 0xffffffffu;
+            for (size_t j = 0; j < 4 && i + j < rows.size(); j++)
+                packed = (packed & ~(0xffu << (8 * j))) | ((uint32_t)rows[i + j] << (8 * j));
+            out.push_back(make_int2(c, (int)packed));
+        }
+    }
+    return out;
+}
+
+extern "C" int32_t rime_split_tiles(int32_t na, int32_t *out, int32_t cap) {
+    if (na < 2 || na > 4096 || cap < 0 || (cap > 0 && !out)) return -1;
+    const std::vector<int2> tl = split_tiles(na);
+    for (int i = 0; i < (int)tl.size() && i < cap; i++) {
+        out[5 * i] = tl[i].x;
+        for (int j = 0; j < 4; j++) {
+            const int g = ((uint32_t)tl[i].y >> (8 * j)) & 0xff;
+            out[5 * i + 1 + j] = g == 0xff ? -1 : g;
+        }
+    }
+    return (int32_t)tl.size();
 }
 
 cudaError_t launch_split(rime_ctx *c, bool write, void *vis_out, double *result) {

@@ -47,6 +47,53 @@ def test_nbl_and_status_strings(L):
     assert L.rime_status_string(1) == b"RIME_E_INVALID"
 
 
+def _split_pair_counts(na, tiles):
+    """How often each baseline p < q is formed by the split kernel's tiles,
+    with its epilogue's rule: within one group p < q only, across groups
+    every (row, column) pair (the tile holds one orientation of the pair)."""
+    cnt = np.zeros((na, na), dtype=np.int64)
+    for c, *rows in tiles:
+        cols = np.arange(32 * c, min(32 * c + 32, na))
+        for r in rows:
+            if r < 0:
+                continue
+            for p in range(32 * r, min(32 * r + 32, na)):
+                q = cols[cols > p] if r == c else cols
+                lo, hi = np.minimum(p, q), np.maximum(p, q)
+                np.add.at(cnt, (lo, hi), 1)
+    return cnt
+
+
+@pytest.mark.parametrize("na", [2, 3, 31, 32, 33, 64, 95, 129, 200, 256, 257, 300])
+def test_split_tile_plan_forms_every_baseline_once(L, na):
+    import paper_1501_07719_gb300 as R
+    tiles = R.rime_split_tiles(na)
+    G = (na + 31) // 32
+    assert tiles.shape[1] == 5 and np.all((tiles >= -1) & (tiles < G))
+    assert np.all(tiles[:, 1] >= 0)                      # slot 0 always holds a group
+    cnt = _split_pair_counts(na, tiles)
+    iu = np.triu_indices(na, 1)
+    assert np.all(cnt[iu] == 1)
+    assert cnt[np.tril_indices(na)].sum() == 0
+
+
+def test_split_tile_plan_counts_and_range(L):
+    import paper_1501_07719_gb300 as R
+    # at least ceil(G (G + 1) / 8) tiles for G groups (G (G - 1) / 2 group pairs plus G own
+    # groups, four per tile), and at least one per column group
+    for na in (256, 512, 1000, 4096):
+        G = (na + 31) // 32
+        n = len(R.rime_split_tiles(na))
+        assert n == -(-G * (G + 1) // 8), na
+    assert len(R.rime_split_tiles(256)) == 9
+    assert len(R.rime_split_tiles(128)) == 4
+    for bad in (1, 0, 4097):
+        assert L.rime_split_tiles(bad, None, 0) == -1
+    assert L.rime_split_tiles(64, None, -1) == -1
+    assert L.rime_split_tiles(64, None, 2) == -1          # out NULL with cap > 0
+    assert L.rime_split_tiles(64, None, 0) == 2
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(na=1), "na"),
     (dict(na=5000), "na"),
