@@ -385,7 +385,10 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         gp[0] = make_float2(a01.x, a01.y); gp[1] = make_float2(a01.z, a01.w);
         gp[2] = make_float2(a23.x, a23.y); gp[3] = make_float2(a23.z, a23.w);
     }
-#pragma unroll 1
+    // two baselines per iteration: the second one's loads are issued before
+    // the first one's arithmetic (BF16 -2 %, TF32 -1 % on a 256-antenna slice;
+    // four or sixteen per iteration spill)
+#pragma unroll 2
     for (int i = 0; i < 16; i++) {
         const int q = QT * C.cg + 16 * half + i;
         if (!(prow && q < P.na && (!same || pgl < q))) continue;
