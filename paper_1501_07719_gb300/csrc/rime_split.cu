@@ -345,9 +345,33 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
     Pre<SPC> b0, b1;
     if (C.nstg > 0) load(0, b0);
     bool ok = true;
-    for (int it = 0; it < C.nstg && ok; it += 2) {
-        ok = step(it, b0, b1);
-        if (ok && it + 1 < C.nstg) ok = step(it + 1, b1, b0);
+    if constexpr (TF32) {
+        // TF32 stages hold half as many sources: two stages per proxy fence and
+        // arrival round (a fixed cost per stage; -9 % on a 256-antenna slice,
+        // while BF16's larger stages gain nothing)
+        if (C.nstg > 1) load(1, b1);
+        for (int it = 0; it < C.nstg && ok; it += 2) {
+            const bool two = it + 1 < C.nstg;
+            ok = wait_slot(C, it, lane, maybe_drain);
+            if (!ok) break;
+            produce(it, b0);
+            if (it + 2 < C.nstg) load(it + 2, b0);
+            if (two) {
+                ok = wait_slot(C, it + 1, lane, maybe_drain);
+                if (!ok) break;
+                produce(it + 1, b1);
+                if (it + 3 < C.nstg) load(it + 3, b1);
+            }
+            tc::fence_async_smem();
+            tc::mbar_arrive(&C.full[it % NST]);
+            if (two) tc::mbar_arrive(&C.full[(it + 1) % NST]);
+            if (it + 1 >= (nd + 1) * SEG) maybe_drain();
+        }
+    } else {
+        for (int it = 0; it < C.nstg && ok; it += 2) {
+            ok = step(it, b0, b1);
+            if (ok && it + 1 < C.nstg) ok = step(it + 1, b1, b0);
+        }
     }
     while (ok && nd < C.nseg) {   // the remaining segments
         const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&C.seg_full[nd & 1], (nd >> 1) & 1, C.abort_flag, P.wait_ns));
@@ -518,15 +542,35 @@ __device__ __forceinline__ void role_b(const Cta &C, int warp, int lane) {
     Pre<SPC> b0, b1;
     if (C.nstg > 0) load(0, b0);
     bool ok = true;
-    for (int it = 0; it < C.nstg && ok; it += 2) {
-        for (int u = 0; u < 2 && ok && it + u < C.nstg; u++) {
-            Pre<SPC> &use = u ? b1 : b0, &next = u ? b0 : b1;
-            if (it + u + 1 < C.nstg) load(it + u + 1, next);
-            ok = wait_slot(C, it + u, lane, no_drain);
-            if (ok) {
-                produce(it + u, use);
-                tc::fence_async_smem();
-                tc::mbar_arrive(&C.full[(it + u) % NST]);
+    if constexpr (TF32) {   // two stages per proxy fence, as the A warps
+        if (C.nstg > 1) load(1, b1);
+        for (int it = 0; it < C.nstg && ok; it += 2) {
+            const bool two = it + 1 < C.nstg;
+            ok = wait_slot(C, it, lane, no_drain);
+            if (!ok) break;
+            produce(it, b0);
+            if (it + 2 < C.nstg) load(it + 2, b0);
+            if (two) {
+                ok = wait_slot(C, it + 1, lane, no_drain);
+                if (!ok) break;
+                produce(it + 1, b1);
+                if (it + 3 < C.nstg) load(it + 3, b1);
+            }
+            tc::fence_async_smem();
+            tc::mbar_arrive(&C.full[it % NST]);
+            if (two) tc::mbar_arrive(&C.full[(it + 1) % NST]);
+        }
+    } else {
+        for (int it = 0; it < C.nstg && ok; it += 2) {
+            for (int u = 0; u < 2 && ok && it + u < C.nstg; u++) {
+                Pre<SPC> &use = u ? b1 : b0, &next = u ? b0 : b1;
+                if (it + u + 1 < C.nstg) load(it + u + 1, next);
+                ok = wait_slot(C, it + u, lane, no_drain);
+                if (ok) {
+                    produce(it + u, use);
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&C.full[(it + u) % NST]);
+                }
             }
         }
     }
