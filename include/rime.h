@@ -217,6 +217,8 @@ typedef enum {
 rime_status rime_set_tensor_mode(rime_ctx *ctx, int32_t mode);
 
 /* The split modes' tile plan for na antennas (host only, no GPU needed).
+ * The paper has no counterpart: it is the work decomposition of the
+ * tensor-core form of Algorithm 2's source sum (rime_set_tensor_mode).
  * Antennas fall into groups of 32 (the last one ragged); one CTA of the split
  * kernel computes, for one (t, k), the products of up to four row groups
  * (128 rows) against one column group. S_X is Hermitian (S_X[q, p] =
