@@ -432,7 +432,6 @@ rime_status rime_chains_propose(rime_ctx *c, int32_t nmove, const rime_sources *
                       proposed->kind ? c->d_pair_kind : nullptr};
     rime_status s = rime_set_sources(c, &pair);
     if (s != RIME_OK) return s;
-    const long long n = (long long)c->dims.ntime * c->nbl * c->dims.nchan * 4;
     const size_t csz = 2 * c->tsize();
     const long long per_chain = (long long)c->dims.ntime * chain_nbx(c);
     for (int k0 = 0; k0 < K; k0 += kMaxList) {
