@@ -332,7 +332,7 @@ __device__ __forceinline__ double role_a(const Cta &C, int tid, int warp, int la
         st16(stg + o_row, h[0], h[1], h[2], h[3]);
         st16(stg + A_BYTES + o_row, l[0], l[1], l[2], l[3]);
     };
-    // Two stages per proxy fence and arrival round (a fixed cost per stage;
+    // Two stages per proxy fence and pair of arrivals (a fixed cost per stage;
     // on a 256-antenna slice BF16 -3.5 %, TF32 -9 % with the B warps paired
     // too); each stage's delays are loaded two stages ahead.
     Pre<SPC> b0, b1;
